@@ -1,0 +1,417 @@
+"""Benchmark: rasterize throughput of the grouped FP16 tensor-core 3DGS path on GB300.
+
+Workload (default): the 1.5M-Gaussian mixture scene (256 clusters, SH degree 3) rendered at
+1600x1064 from 8 orbit cameras. One step = the whole hot path (preprocess, bin + sort,
+rasterize) for all 8 cameras. `value` = megapixels per second over the timed steps with the scene
+resident in HBM; `e2e` = the same metric with the scene copied host -> device and the 8 images
+copied back every step, through the public API.
+
+Also reported: p50/p99 frame latency, the FP32 CUDA-core rasterizer (1x1 tiles, the plain tile
+rasterizer) on the same GPU, the per-stage split, the roofline of the dominant kernel (the
+tensor-core rasterizer) and, on rank 0 at N=1, the FP64 CPU oracle on a bounded sample (which also
+gives the PSNR of the sampled pixels against the oracle).
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Multi-GPU (launched with torch.distributed.run): every rank renders the 8 cameras of its own copy
+of the scene (independent frames, no collective on the data path): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "rasterize Mpx/s & p99 frame ms, FP16-TC vs FP32-core, PSNR>=45dB vs oracle"
+UNIT = "Mpx/s"
+MUFU_PER_SM_PER_CLK = 16  # ex2 results per SM per clock (special-function units)
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": SM_MAX_MHZ}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, on a bounded sample of the same workload.
+
+def cpu_baseline(scene, cam, tc_image=None, target_s=12.0, seed=0):
+    """Oracle preprocess + bin sort of the whole frame, and the blend of a sample of tile groups
+    (random groups, grown until about `target_s` of blending); frame time is extrapolated by pixel
+    count. Returns (record, psnr_of_gpu_image_on_the_sample)."""
+    import oracle
+    t0 = time.perf_counter()
+    pr = oracle.preprocess(scene, cam)
+    t1 = time.perf_counter()
+    bins = oracle.bin_sort(pr.mean2d, pr.radius, pr.depth, cam.width, cam.height, 2, 2)
+    t2 = time.perf_counter()
+    TX, TY, GX, GY = oracle.group_grid(cam.width, cam.height, 2, 2)
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(GX * GY)
+    pix_done, blend_s, k = 0, 0.0, 0
+    ref_list, pix_list = [], []
+    batch = 8
+    while k < len(order) and blend_s < target_s:
+        gs = order[k: k + batch]
+        k += len(gs)
+        pix = []
+        for g in gs:
+            gx, gy = g % GX, g // GX
+            xs = np.arange(gx * 32, min(gx * 32 + 32, cam.width))
+            ys = np.arange(gy * 32, min(gy * 32 + 32, cam.height))
+            X, Y = np.meshgrid(xs, ys)
+            pix.append(np.stack([X.ravel(), Y.ravel()], 1))
+        pix = np.concatenate(pix)
+        tb = time.perf_counter()
+        img = oracle.blend(cam.width, cam.height, pr.mean2d, pr.conic, pr.opacity, pr.rgb, bins, pixels=pix)
+        blend_s += time.perf_counter() - tb
+        pix_done += len(pix)
+        ref_list.append(img.rgb)
+        pix_list.append(pix)
+        batch = min(batch * 2, 256)
+    frame_s = (t1 - t0) + (t2 - t1) + blend_s * (cam.width * cam.height) / max(pix_done, 1)
+    psnr = None
+    if tc_image is not None:
+        pix = np.concatenate(pix_list)
+        ref = np.concatenate(ref_list)
+        got = tc_image[:, pix[:, 1], pix[:, 0]].T
+        import oracle as _o
+        psnr = _o.psnr(got, ref)
+    rec = {"value": round(cam.width * cam.height / frame_s / 1e6, 6), "unit": UNIT,
+           "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": (f"1 frame of camera 0: full preprocess ({(t1 - t0):.2f}s) + bin sort ({(t2 - t1):.2f}s)"
+                      f" of {scene.n} splats; blend of {k} random 2x2 tile groups ({pix_done} px, "
+                      f"{blend_s:.2f}s) extrapolated to {cam.width}x{cam.height}")}
+    return rec, psnr
+
+
+# ------------------------------------------------------------------------------------------------
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle timed on the host cores (bounded sample per step)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_2605_17855_gb300 import scenes
+    scene, cams = scenes.config_c2()
+    cam = cams[0]
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state
+    vals, times = [], []
+    for k in range(args.steps):
+        t = time.perf_counter()
+        rec, _ = cpu_baseline(scene, cam, target_s=args.ref_sample_s, seed=k)
+        times.append(time.perf_counter() - t)
+        vals.append(rec["value"])
+    value = float(np.mean(vals))
+    frame_ms = cam.width * cam.height / (value * 1e6) * 1e3
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(8 * frame_ms, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": _config(scene, cams, args),
+           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": rec["cores"], "kind": "oracle",
+                            "sample": rec["sample"]},
+           "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def _config(scene, cams, args):
+    return {"workload": f"mixture scene, {scene.n} Gaussians (256 clusters, SH degree 3), "
+                        f"{len(cams)} orbit cameras at {cams[0].width}x{cams[0].height}",
+            "splats": scene.n, "cameras": len(cams), "width": cams[0].width, "height": cams[0].height,
+            "tiling": args.tiling, "precision": args.precision,
+            "l2": "inputs larger than L2 (scene %.0f MB read every frame)" % (scene.nbytes / 1e6)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tgs", choices=["tgs", "reference"])
+    ap.add_argument("--precision", default="fp16_tc", choices=["fp16_tc", "fp32"])
+    ap.add_argument("--tiling", default="2x2")
+    ap.add_argument("--splats", type=int, default=1_500_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-s", type=float, default=12.0)
+    ap.add_argument("--ref-sample-s", type=float, default=8.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import paper_2605_17855_gb300 as tgs
+    from paper_2605_17855_gb300 import scenes
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    tiling = tuple(int(v) for v in args.tiling.split("x"))
+
+    scene, cams = scenes.config_c2(n=args.splats)
+    H, W = cams[0].height, cams[0].width
+    ds = tgs.DeviceScene.from_host(scene)
+    proj = tgs.Projected.empty(scene.n)
+    # size one bin buffer for the largest camera frame (one synchronous count per camera)
+    cap, cap32 = 0, 0
+    for cam in cams:
+        tgs.preprocess(ds, cam, out=proj)
+        cap = max(cap, tgs.bin_sort(proj, W, H, tiling).entries)
+        cap32 = max(cap32, tgs.bin_sort(proj, W, H, (1, 1)).entries)
+    bins = tgs.allocate_bins(scene.n, int(cap * 1.05) + 4096, W, H, tiling, keys=False)
+    bins32 = tgs.allocate_bins(scene.n, int(cap32 * 1.05) + 4096, W, H, (1, 1), keys=False)
+    imgs = [(torch.empty((3, H, W), device="cuda"), torch.empty((H, W), device="cuda")) for _ in cams]
+    stream = torch.cuda.current_stream()
+
+    def frame(cam, out, prec, bn, til_events=None):
+        tgs.preprocess(ds, cam, out=proj)
+        tgs.bin_sort(proj, W, H, bn.tiling, bins=bn, sync=False)
+        if til_events is not None:
+            til_events[0].record(stream)
+        tgs.rasterize(proj, bn, W, H, prec, out=(out[0], out[1], None), want_n_contrib=False)
+        if til_events is not None:
+            til_events[1].record(stream)
+
+    def step(prec, bn, frame_events=None, raster_events=None):
+        for i, cam in enumerate(cams):
+            if frame_events is not None:
+                frame_events[i][0].record(stream)
+            frame(cam, imgs[i], prec, bn, raster_events[i] if raster_events is not None else None)
+            if frame_events is not None:
+                frame_events[i][1].record(stream)
+
+    def timed(prec, bn, steps, warmup):
+        for _ in range(warmup):
+            step(prec, bn)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+        fr = [[(ev(), ev()) for _ in cams] for _ in range(steps)]
+        rs = [[(ev(), ev()) for _ in cams] for _ in range(steps)]
+        launches0 = tgs.kernel_launch_count()
+        t0, t1 = ev(), ev()
+        t0.record(stream)
+        for k in range(steps):
+            step(prec, bn, fr[k], rs[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        launches = tgs.kernel_launch_count() - launches0
+        total_ms = t0.elapsed_time(t1)
+        if dist:
+            tt = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            total_ms = float(tt.item())
+            dist.barrier()
+        frames = np.array([a.elapsed_time(b) for row in fr for a, b in row])
+        raster = np.array([a.elapsed_time(b) for row in rs for a, b in row])
+        return total_ms, frames, raster, launches
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    total_ms, frames_ms, raster_ms, launches = timed(args.precision, bins, args.steps, args.warmup)
+    clocks = sampler.stop()
+    ms_per_step = total_ms / args.steps
+    px_per_step = len(cams) * W * H
+    value = ws * px_per_step / (ms_per_step * 1e-3) / 1e6
+    # FP32 CUDA-core rasterizer, 1x1 tiles: the plain tile rasterizer, same scene and GPU
+    tot32, frames32, raster32, _ = timed("fp32", bins32, max(2, args.steps // 2), 3)
+    value32 = ws * px_per_step / (tot32 / max(2, args.steps // 2) * 1e-3) / 1e6
+
+    # per-stage split of one frame (untimed by the main loop)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    e = [ev() for _ in range(4)]
+    e[0].record(stream)
+    tgs.preprocess(ds, cams[0], out=proj)
+    e[1].record(stream)
+    tgs.bin_sort(proj, W, H, tiling, bins=bins, sync=False)
+    e[2].record(stream)
+    tgs.rasterize(proj, bins, W, H, args.precision, out=(imgs[0][0], imgs[0][1], None), want_n_contrib=False)
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    stages = {"preprocess_ms": round(e[0].elapsed_time(e[1]), 4), "bin_sort_ms": round(e[1].elapsed_time(e[2]), 4),
+              "rasterize_ms": round(e[2].elapsed_time(e[3]), 4)}
+
+    # algorithmic work of the dominant kernel: evaluated pairs and exponentials per launch
+    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+    for cam in cams:
+        tgs.preprocess(ds, cam, out=proj)
+        tgs.bin_sort(proj, W, H, tiling, bins=bins, sync=False)
+        tgs.rasterize(proj, bins, W, H, args.precision, out=(imgs[0][0], imgs[0][1], None),
+                      want_n_contrib=False, counters=cnt)
+    torch.cuda.synchronize()
+    pairs, exps = [int(v) / len(cams) for v in cnt.cpu().tolist()]
+    entries = int(bins.num_entries.item())
+
+    # end to end through the public API: scene H2D from pinned memory, 8 images D2H to pinned memory
+    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32)).pin_memory()
+            for k in ("means", "scales", "quats", "opacities", "sh")}
+    host_imgs = [torch.empty((3, H, W), dtype=torch.float32).pin_memory() for _ in cams]
+    h2d = sum(t.numel() * 4 for t in host.values())
+    d2h = sum(t.numel() * 4 for t in host_imgs)
+
+    def e2e_step():
+        for k, t in host.items():
+            getattr(ds, k).copy_(t, non_blocking=True)
+        for i, cam in enumerate(cams):
+            frame(cam, imgs[i], args.precision, bins)
+            host_imgs[i].copy_(imgs[i][0], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(2, args.steps // 2)
+    a, b = ev(), ev()
+    a.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = a.elapsed_time(b) / e2e_steps
+    if dist:
+        tt = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e_value = ws * px_per_step / (e2e_ms * 1e-3) / 1e6
+
+    peaks, peak_kind = _peaks()
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", SM_MAX_MHZ)
+    mufu_peak = SM_COUNT * MUFU_PER_SM_PER_CLK * peaks.get("sm_max_mhz", SM_MAX_MHZ) * 1e6 / 1e9  # Gexp/s
+    raster_avg_ms = float(raster_ms.mean())
+    achieved = exps / (raster_avg_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "kernel": "k_raster_tc" if args.precision == "fp16_tc" else "k_raster_fp32",
+                "achieved": round(achieved, 3), "peak": round(mufu_peak, 1), "unit": "Gexp/s",
+                "frac": round(achieved / mufu_peak, 4), "traffic": None,
+                "peak_source": f"derived: {SM_COUNT} SMs x {MUFU_PER_SM_PER_CLK} MUFU ex2/clk x "
+                               f"{peaks.get('sm_max_mhz', SM_MAX_MHZ):.0f} MHz ({peak_kind} max clock)",
+                "work_per_launch": {"exp_evaluations": exps, "evaluated_pairs": pairs,
+                                    "group_entries": entries},
+                "avg_launch_ms": round(raster_avg_ms, 4),
+                "pair_rate_gps": round(pairs / (raster_avg_ms * 1e-3) / 1e9, 2)}
+
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f16 products, f32 accumulate/blend" if args.precision == "fp16_tc" else "f32",
+           "data": "synthetic", "config": _config(scene, cams, args),
+           "frame_ms": {"mean": round(float(frames_ms.mean()), 4), "p50": round(float(np.percentile(frames_ms, 50)), 4),
+                        "p99": round(float(np.percentile(frames_ms, 99)), 4)},
+           "fps": round(1000.0 / float(frames_ms.mean()), 2),
+           "fp32_core_1x1": {"value": round(value32, 3), "unit": UNIT,
+                             "frame_ms_p99": round(float(np.percentile(frames32, 99)), 4),
+                             "rasterize_ms_mean": round(float(raster32.mean()), 4)},
+           "speedup_vs_fp32_core": round(value / value32, 3),
+           "rasterize_speedup_vs_fp32_core": round(float(raster32.mean()) / raster_avg_ms, 3),
+           "stages": stages,
+           "evals_per_s": round(pairs * len(cams) / (ms_per_step * 1e-3), 1),
+           "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4)},
+           "gpu_launches": int(launches),
+           "clocks": clocks,
+           "roofline": roofline}
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        tgs.preprocess(ds, cams[0], out=proj)
+        tgs.bin_sort(proj, W, H, tiling, bins=bins, sync=False)
+        rgb, _, _ = tgs.rasterize(proj, bins, W, H, args.precision, want_n_contrib=False)
+        rec, psnr = cpu_baseline(scene, cams[0], tc_image=rgb.cpu().numpy(), target_s=args.cpu_sample_s)
+        out["cpu_baseline"] = rec
+        out["psnr_vs_oracle_sampled"] = round(psnr, 3) if psnr is not None and math.isfinite(psnr) else psnr
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

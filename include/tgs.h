@@ -1,0 +1,186 @@
+/* tgs.h -- C ABI of a GB300 (sm_103a) tensor-core 3D Gaussian Splatting rasterizer.
+ *
+ * The operations follow "Accelerating 3D Gaussian Splatting using Tensor Cores" (TensorGS):
+ *   tgs_preprocess          Section 2 "Frustum culling" and "Feature computation"; Algorithm 1,
+ *                           "Frustum-cull visible Gaussians" and "Compute screen-space attributes".
+ *   tgs_bin_sort            Section 2 "Gaussian sorting" with the grouped list of Section 4.4.2
+ *                           ("Constructing the grouped Gaussian list"); Algorithm 1, the per-group
+ *                           entry generation with tile-membership masks and the sort by
+ *                           (group ID, depth).
+ *   tgs_rasterize           Section 2 "Rasterization" (Eqs. power_d, power, alpha, blend, pruning
+ *                           and early termination), tensorized as in Section 4.2 and grouped as in
+ *                           Section 4.4.2; Algorithm 1, the per-group CTA loop.
+ *   tgs_rasterize_backward  Gradients of the blend of Section 2 (the paper trains Gaussian models,
+ *                           Section 3.2.1, but prints no backward; the chain rule of the forward).
+ *   tgs_serve_*             A multi-scene rendering service built on the three calls above (the
+ *                           paper motivates frame-latency budgets in Section 1; it has no server).
+ *
+ * Conventions shared by every call:
+ *   - Every function returns a tgs_status; TGS_OK is 0. No C++ exception crosses the ABI.
+ *   - Argument errors are reported synchronously, before any work is enqueued. Errors of kernels
+ *     surface from the CUDA runtime at a later call or stream synchronization.
+ *   - Device pointers are caller-owned, contiguous, row-major. Floating point is FP32 unless stated.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). All work is enqueued on it;
+ *     no call synchronizes the stream unless its comment says so.
+ *   - The library allocates device memory only inside objects it creates (tgs_server), plus one
+ *     4-byte device error word per device on first use. The bin sort takes a caller-provided
+ *     workspace sized by tgs_bin_sort_workspace_size.
+ *   - The image is sampled at integer pixel coordinates: pixel (i, j) is at (x, y) = (i, j).
+ *     Tiles are 16x16 pixels. A tile group is group_w x group_h tiles (1x1 up to 4x4).
+ */
+#ifndef TGS_H
+#define TGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TGS_ABI_VERSION 1
+#define TGS_TILE 16
+#define TGS_MAX_GROUP 4
+
+typedef int32_t tgs_status;
+#define TGS_OK 0
+#define TGS_ERR_INVALID_ARGUMENT 1  /* a pointer, size or option is out of range */
+#define TGS_ERR_CUDA 2              /* a CUDA runtime call failed; see tgs_last_error_message */
+#define TGS_ERR_CAPACITY 3          /* more bin entries than the caller's capacity */
+#define TGS_ERR_UNSUPPORTED_DEVICE 4 /* the current device is not compute capability 10.3 */
+#define TGS_ERR_TIMEOUT 5           /* a bounded wait expired (device pipeline or service) */
+#define TGS_ERR_BUSY 6              /* the service cannot admit the request now */
+#define TGS_ERR_NOT_FOUND 7         /* unknown scene id or ticket */
+
+/* Precision of the rasterizer's exponent evaluation (the "power" of Eq. power). */
+#define TGS_PRECISION_FP32 0    /* scalar FP32 on the CUDA cores (the plain tile rasterizer) */
+#define TGS_PRECISION_FP16_TC 1 /* FP16 x FP16 -> FP32 product on the tensor cores (tcgen05) */
+
+typedef struct {
+  int64_t n;              /* number of Gaussians */
+  int32_t sh_degree;      /* 0..3 */
+  const float* means;     /* [n,3] world-space means */
+  const float* scales;    /* [n,3] linear standard deviations along the local axes */
+  const float* quats;     /* [n,4] rotation quaternions (w, x, y, z); normalized inside */
+  const float* opacities; /* [n]   opacity in (0, 1) */
+  const float* sh;        /* [n,(sh_degree+1)^2,3] SH coefficients, index l*l + m + l */
+} tgs_scene;
+
+typedef struct {
+  int32_t width, height;  /* image size in pixels, 1..16384 each */
+  float fx, fy, cx, cy;   /* pinhole intrinsics: u = fx x/z + cx, v = fy y/z + cy */
+  float R[9];             /* world -> camera rotation, row-major (camera x right, y down, z fwd) */
+  float t[3];             /* world -> camera translation: p_cam = R p_world + t */
+  float cam_pos[3];       /* camera centre in world coordinates (SH view direction origin) */
+  float near_z;           /* Gaussians with camera-space z <= near_z are culled */
+} tgs_camera;
+
+typedef struct {
+  int32_t group_w, group_h; /* tiles per group along x and y, each 1..TGS_MAX_GROUP */
+} tgs_tiling;
+
+/* Projected Gaussians: caller-allocated device arrays of length n (written by tgs_preprocess,
+ * read by tgs_bin_sort / tgs_rasterize / tgs_rasterize_backward). */
+typedef struct {
+  float* mean2d;        /* [n,2] projected mean mu' in pixels */
+  float* conic_opacity; /* [n,4] (a, b, c, o): inverse projected covariance [[a,b],[b,c]], opacity */
+  float* rgb;           /* [n,3] SH colour, clamped at 0 */
+  float* depth;         /* [n]   camera-space z */
+  int32_t* radius;      /* [n]   ceil(3 sqrt(lambda_max)) in pixels; 0 = culled */
+  int32_t* rect;        /* [n,4] overlapped tile range (tx0, ty0, tx1, ty1), max exclusive */
+} tgs_projected;
+
+/* Sorted group-level entries (Section 4.4.2). Arrays are caller-allocated device memory. */
+typedef struct {
+  int64_t capacity;     /* number of entries keys/vals/masks can hold (< 2^32) */
+  uint64_t* keys;       /* [capacity] (group id << 32) | bits(float depth), ascending; may be NULL */
+  uint32_t* vals;       /* [capacity] Gaussian index of each entry */
+  uint16_t* masks;      /* [capacity] tile-membership bits, bit (ty%gh)*gw + (tx%gw) */
+  uint32_t* ranges;     /* [num_groups,2] [start, end) per group, row-major groups; (0,0) if empty */
+  int64_t* num_entries; /* device scalar: entries needed by this frame (may exceed capacity) */
+} tgs_bins;
+
+typedef struct {
+  int32_t precision;    /* TGS_PRECISION_* */
+  float bg[3];          /* background colour added as T_final * bg */
+  int64_t* counters;    /* optional device [2] int64, accumulated: [0] evaluated (pixel, entry)
+                           pairs before termination (mask bit set), [1] of those, the pairs with
+                           alpha >= 1/255 (each needs one exp); NULL = not counted */
+} tgs_raster_opts;
+
+/* ---------------------------------------------------------------------------------------------- */
+
+const char* tgs_status_string(tgs_status s);
+/* Last error message of the calling host thread ("" if none). Valid until the next call. */
+const char* tgs_last_error_message(void);
+int32_t tgs_abi_version(void);
+/* TGS_OK if `device` is a compute capability 10.3 GPU this library was built for. */
+tgs_status tgs_check_device(int32_t device);
+
+/* Preprocess (Section 2: frustum culling, feature computation; Section 4.2.1: conic).
+ * Per Gaussian: camera-space mean; cull if z <= near_z; EWA projection of the 3D covariance with the
+ * Jacobian taken at x/z, y/z clamped to +-1.3 tan(half FOV); 2D covariance + 0.3 I; conic = its
+ * inverse (near-degenerate covariances, det < 2^-5 Sxx Syy, are recomputed in FP64); radius =
+ * ceil(3 sqrt(lambda_max)); tile range of the AABB [mu'-r, mu'+r]^2 (tiles holding an image pixel
+ * inside it; empty -> culled); SH colour + 0.5 clamped at 0. Culled entries get radius 0.
+ * Errors: INVALID_ARGUMENT for NULL pointers with n > 0, n < 0, sh_degree outside 0..3, bad camera. */
+tgs_status tgs_preprocess(const tgs_scene* scene, const tgs_camera* cam, tgs_projected* out,
+                          void* stream);
+
+/* Workspace bytes tgs_bin_sort needs for n Gaussians, `capacity` entries and the image/tiling. */
+tgs_status tgs_bin_sort_workspace_size(int64_t n, int64_t capacity, int32_t width, int32_t height,
+                                       const tgs_tiling* tiling, size_t* bytes);
+
+/* Bin and sort (Section 4.4.2; Algorithm 1): one entry per (Gaussian, overlapped tile group) with
+ * the mask of the group's member tiles inside the Gaussian's tile range, sorted ascending by
+ * (group id, float depth, Gaussian index) -- the 64-bit key (gid << 32) | depth bits with ties by
+ * index. Fills keys (if non-NULL), vals, masks, ranges and *num_entries. If the frame needs more
+ * than `capacity` entries, nothing is emitted, every range is (0, 0) and *num_entries holds the
+ * needed count. If num_entries_host != NULL the call copies the count to it, synchronizes `stream`
+ * and returns TGS_ERR_CAPACITY on overflow; otherwise it is fully asynchronous.
+ * `workspace` is device memory of at least tgs_bin_sort_workspace_size bytes, 256-byte aligned. */
+tgs_status tgs_bin_sort(const tgs_projected* proj, int64_t n, int32_t width, int32_t height,
+                        const tgs_tiling* tiling, void* workspace, size_t workspace_bytes,
+                        tgs_bins* bins, int64_t* num_entries_host, void* stream);
+
+/* Rasterize (Section 2 Eqs. power_d..blend; Section 4.2 tensorization; Section 4.4.2 grouping).
+ * One CTA per tile group walks the group's sorted list in chunks; per pixel, in list order,
+ * entries whose mask bit for the pixel's tile is set: power = -1/2 d^T conic d with d = x - mu';
+ * alpha = min(0.99, o exp(power)); skip if alpha < 1/255; T' = T (1 - alpha); if T' < 1e-4 the
+ * pixel stops without blending this entry; else C += alpha T rgb, T = T'.
+ * FP16_TC evaluates log2(o) + log2(e) power as a product of pixel features [x^2, xy, y^2, x, y, 1]
+ * (relative to the tile centre, exact in FP16) with per-Gaussian coefficients split hi + lo in FP16,
+ * padded to K = 16, accumulated in FP32 in tensor memory; exp and blending are FP32.
+ * Outputs (device, caller-allocated): out_rgb [3,H,W] = C + T bg; out_T [H,W] = final T;
+ * n_contrib [H,W] = 1-based position in the group list of the last blended entry (0 = none), may be
+ * NULL. Errors: INVALID_ARGUMENT for bad sizes/tiling/precision; UNSUPPORTED_DEVICE for FP16_TC on a
+ * device other than sm_103; TIMEOUT can be recorded by the device pipeline (read with
+ * tgs_last_device_error after synchronizing). */
+tgs_status tgs_rasterize(const tgs_projected* proj, int64_t n, const tgs_bins* bins, int32_t width,
+                         int32_t height, const tgs_tiling* tiling, const tgs_raster_opts* opts,
+                         float* out_rgb, float* out_T, int32_t* n_contrib, void* stream);
+
+/* Backward of tgs_rasterize for L = sum(out_rgb * grad_rgb): replays each pixel's list backwards
+ * from n_contrib, recovering T_i = T_{i+1} / (1 - alpha_i) from the stored final T. Outputs are
+ * overwritten (the call zeroes them first): g_mean2d [n,2] (d/d mu' in pixels), g_conic_opacity
+ * [n,4] (d/da, d/db, d/dc, d/do), g_rgb [n,3]. Inputs are those of the forward call plus its
+ * out_T and n_contrib. FP32 arithmetic; the forward must have been run in the same precision. */
+tgs_status tgs_rasterize_backward(const tgs_projected* proj, int64_t n, const tgs_bins* bins,
+                                  int32_t width, int32_t height, const tgs_tiling* tiling,
+                                  const tgs_raster_opts* opts, const float* out_T,
+                                  const int32_t* n_contrib, const float* grad_rgb,
+                                  float* g_mean2d, float* g_conic_opacity, float* g_rgb,
+                                  void* stream);
+
+/* Number of CUDA kernels this library has launched in this process (all devices, all threads).
+ * A diagnostic for counting the kernels of a timed region. */
+int64_t tgs_kernel_launch_count(void);
+
+/* Device-side error word of the library on the current device (TGS_OK or TGS_ERR_TIMEOUT), set by
+ * a kernel whose bounded wait expired. Synchronizes the device. reset != 0 clears it. */
+tgs_status tgs_last_device_error(int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TGS_H */

@@ -198,6 +198,7 @@ class Image:
     margin: np.ndarray     # [H, W] smallest relative distance of a threshold decision
     evaluated: int         # (pixel, entry) pairs evaluated before termination
     guard: int             # power > 0 firings (expected 0)
+    passing: int = 0       # evaluated pairs with alpha >= 1/255 (one exponential each)
 
 
 def blend(width, height, mean2d, conic, opacity, rgb, bins: Bins, bg=(0.0, 0.0, 0.0), pixels=None) -> Image:
@@ -218,12 +219,12 @@ def blend(width, height, mean2d, conic, opacity, rgb, bins: Bins, bg=(0.0, 0.0, 
     T = np.zeros(npix)
     nc = np.zeros(npix, np.int32)
     mg = np.zeros(npix)
-    counters = np.zeros(2, np.int64)
+    counters = np.zeros(3, np.int64)
     lib.orc_blend(width, height, bins.gw, bins.gh, _ptr(mean2d), _ptr(conic), _ptr(opacity), _ptr(rgb),
                   _ptr(vals), _ptr(masks), _ptr(ranges), _ptr(bgv), _ptr(pix), npix, _ptr(out), _ptr(T),
                   _ptr(nc), _ptr(mg), _ptr(counters))
     return Image(out.reshape(*shape, 3), T.reshape(shape), nc.reshape(shape), mg.reshape(shape),
-                 int(counters[0]), int(counters[1]))
+                 int(counters[0]), int(counters[1]), int(counters[2]))
 
 
 @dataclass

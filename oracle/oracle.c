@@ -338,8 +338,8 @@ void orc_blend(int32_t width, int32_t height, int32_t gw, int32_t gh, const doub
   int32_t TX, TY, GX, GY;
   group_grid(width, height, gw, gh, &TX, &TY, &GX, &GY);
   const int64_t count = pix ? npix : (int64_t)width * height;
-  int64_t evaluated = 0, guard = 0;
-#pragma omp parallel for schedule(dynamic, 64) reduction(+ : evaluated, guard)
+  int64_t evaluated = 0, guard = 0, passing = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : evaluated, guard, passing)
   for (int64_t p = 0; p < count; ++p) {
     const int32_t x = pix ? pix[2 * p] : (int32_t)(p % width);
     const int32_t y = pix ? pix[2 * p + 1] : (int32_t)(p / width);
@@ -365,6 +365,7 @@ void orc_blend(int32_t width, int32_t height, int32_t gw, int32_t gh, const doub
       const double alpha = dmin(0.99, oe);
       mg = dmin(mg, fabs(oe * 255.0 - 1.0));
       if (alpha < 1.0 / 255.0) continue; /* prune a negligible contribution */
+      ++passing;
       const double Tn = T * (1.0 - alpha);
       mg = dmin(mg, fabs(Tn / 1e-4 - 1.0));
       if (Tn < 1e-4) break; /* early termination: this entry is not blended */
@@ -379,6 +380,7 @@ void orc_blend(int32_t width, int32_t height, int32_t gw, int32_t gh, const doub
   }
   counters[0] += evaluated;
   counters[1] += guard;
+  counters[2] += passing;
 }
 
 /* --------------------------------------------------------------------------------------------

@@ -64,7 +64,8 @@ void orc_bin(int64_t n, const double* mean2d, const int32_t* radius, const doubl
  * early termination). If pix != NULL only the npix listed pixels (x, y pairs) are computed and the
  * outputs are indexed by list position; otherwise all pixels, row-major.
  * margin = smallest relative distance of any threshold decision from its threshold (1 = none).
- * counters[0] += evaluated (pixel, entry) pairs; counters[1] += power > 0 guard firings. */
+ * counters[0] += evaluated (pixel, entry) pairs; counters[1] += power > 0 guard firings;
+ * counters[2] += evaluated pairs with alpha >= 1/255 (those that need the exponential). */
 void orc_blend(int32_t width, int32_t height, int32_t gw, int32_t gh, const double* mean2d,
                const double* conic, const double* opacity, const double* rgb, const uint32_t* vals,
                const uint16_t* masks, const uint32_t* ranges, const double bg[3],

@@ -1,0 +1,369 @@
+"""Python binding of libtgs, the GB300 tensor-core 3D Gaussian Splatting rasterizer.
+
+Argument marshalling only: every step of the rendering path runs in the library's CUDA kernels.
+PyTorch provides device memory and streams. The names mirror include/tgs.h:
+
+    preprocess(scene, camera)                  -> Projected         (tgs_preprocess)
+    bin_sort(proj, width, height, tiling)      -> Bins              (tgs_bin_sort)
+    rasterize(proj, bins, width, height, ...)  -> (rgb, T, n_contrib) (tgs_rasterize)
+    rasterize_backward(...)                    -> gradients         (tgs_rasterize_backward)
+    render(scene, camera, ...)                 -> the three forward calls in sequence
+    RasterizeFn                                -> torch.autograd.Function over rasterize
+
+There is no CPU fallback: if the library cannot be built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+TILE = 16
+PRECISION = {"fp32": 0, "fp16_tc": 1}
+
+TGS_OK = 0
+TGS_ERR_CAPACITY = 3
+
+
+class TgsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} [status {status}]")
+        self.status = status
+
+
+# ------------------------------------------------------------------------------------------------
+# ctypes mirrors of include/tgs.h
+
+class _Scene(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("means", C.c_void_p), ("scales", C.c_void_p),
+                ("quats", C.c_void_p), ("opacities", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class _Camera(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("R", C.c_float * 9), ("t", C.c_float * 3),
+                ("cam_pos", C.c_float * 3), ("near_z", C.c_float)]
+
+
+class _Tiling(C.Structure):
+    _fields_ = [("group_w", C.c_int32), ("group_h", C.c_int32)]
+
+
+class _Projected(C.Structure):
+    _fields_ = [("mean2d", C.c_void_p), ("conic_opacity", C.c_void_p), ("rgb", C.c_void_p),
+                ("depth", C.c_void_p), ("radius", C.c_void_p), ("rect", C.c_void_p)]
+
+
+class _Bins(C.Structure):
+    _fields_ = [("capacity", C.c_int64), ("keys", C.c_void_p), ("vals", C.c_void_p), ("masks", C.c_void_p),
+                ("ranges", C.c_void_p), ("num_entries", C.c_void_p)]
+
+
+class _RasterOpts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("bg", C.c_float * 3), ("counters", C.c_void_p)]
+
+
+_P = C.c_void_p
+_lib = None
+_lock = threading.Lock()
+
+# name -> (restype, argtypes) of every exported function
+SIGNATURES = {
+    "tgs_status_string": (C.c_char_p, [C.c_int32]),
+    "tgs_last_error_message": (C.c_char_p, []),
+    "tgs_abi_version": (C.c_int32, []),
+    "tgs_check_device": (C.c_int32, [C.c_int32]),
+    "tgs_preprocess": (C.c_int32, [C.POINTER(_Scene), C.POINTER(_Camera), C.POINTER(_Projected), _P]),
+    "tgs_bin_sort_workspace_size": (C.c_int32, [C.c_int64, C.c_int64, C.c_int32, C.c_int32,
+                                                C.POINTER(_Tiling), C.POINTER(C.c_size_t)]),
+    "tgs_bin_sort": (C.c_int32, [C.POINTER(_Projected), C.c_int64, C.c_int32, C.c_int32, C.POINTER(_Tiling),
+                                 _P, C.c_size_t, C.POINTER(_Bins), C.POINTER(C.c_int64), _P]),
+    "tgs_rasterize": (C.c_int32, [C.POINTER(_Projected), C.c_int64, C.POINTER(_Bins), C.c_int32, C.c_int32,
+                                  C.POINTER(_Tiling), C.POINTER(_RasterOpts), _P, _P, _P, _P]),
+    "tgs_rasterize_backward": (C.c_int32, [C.POINTER(_Projected), C.c_int64, C.POINTER(_Bins), C.c_int32,
+                                           C.c_int32, C.POINTER(_Tiling), C.POINTER(_RasterOpts), _P, _P,
+                                           _P, _P, _P, _P, _P]),
+    "tgs_last_device_error": (C.c_int32, [C.c_int32]),
+    "tgs_kernel_launch_count": (C.c_int64, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libtgs.so (building it first if its sources are newer). Raises if that fails."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_needed else _build.LIB
+            lib = C.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != TGS_OK:
+        lib = load()
+        raise TgsError(status, f"{lib.tgs_status_string(status).decode()}: "
+                               f"{lib.tgs_last_error_message().decode()}")
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ------------------------------------------------------------------------------------------------
+# Inputs
+
+@dataclass
+class DeviceScene:
+    means: "object"      # torch [n,3] float32
+    scales: "object"
+    quats: "object"
+    opacities: "object"
+    sh: "object"
+    sh_degree: int
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @classmethod
+    def from_host(cls, scene, device="cuda", pin: bool = False, non_blocking: bool = False):
+        def t(a):
+            x = torch.from_numpy(np.ascontiguousarray(a, np.float32))
+            if pin:
+                x = x.pin_memory()
+            return x.to(device, non_blocking=non_blocking)
+        return cls(t(scene.means), t(scene.scales), t(scene.quats), t(scene.opacities), t(scene.sh),
+                   int(scene.sh_degree))
+
+    def struct(self) -> _Scene:
+        return _Scene(self.n, self.sh_degree, _ptr(self.means), _ptr(self.scales), _ptr(self.quats),
+                      _ptr(self.opacities), _ptr(self.sh))
+
+
+def camera_struct(cam) -> _Camera:
+    c = _Camera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    R = np.asarray(cam.R, np.float32).reshape(9)
+    for k in range(9):
+        c.R[k] = float(R[k])
+    t = np.asarray(cam.t, np.float32).reshape(3)
+    p = np.asarray(cam.cam_pos, np.float32).reshape(3)
+    for k in range(3):
+        c.t[k] = float(t[k])
+        c.cam_pos[k] = float(p[k])
+    c.near_z = float(cam.near)
+    return c
+
+
+def _tiling(tiling) -> _Tiling:
+    gw, gh = tiling
+    return _Tiling(int(gw), int(gh))
+
+
+def group_grid(width, height, tiling):
+    gw, gh = tiling
+    tx, ty = (width + TILE - 1) // TILE, (height + TILE - 1) // TILE
+    return (tx + gw - 1) // gw, (ty + gh - 1) // gh
+
+
+# ------------------------------------------------------------------------------------------------
+# tgs_preprocess
+
+@dataclass
+class Projected:
+    n: int
+    mean2d: "object"         # [n,2] float32
+    conic_opacity: "object"  # [n,4] float32
+    rgb: "object"            # [n,3] float32
+    depth: "object"          # [n] float32
+    radius: "object"         # [n] int32
+    rect: "object"           # [n,4] int32
+
+    @classmethod
+    def empty(cls, n, device="cuda"):
+        f = dict(dtype=torch.float32, device=device)
+        i = dict(dtype=torch.int32, device=device)
+        return cls(n, torch.empty((n, 2), **f), torch.empty((n, 4), **f), torch.empty((n, 3), **f),
+                   torch.empty((n,), **f), torch.empty((n,), **i), torch.empty((n, 4), **i))
+
+    def struct(self) -> _Projected:
+        return _Projected(_ptr(self.mean2d), _ptr(self.conic_opacity), _ptr(self.rgb), _ptr(self.depth),
+                          _ptr(self.radius), _ptr(self.rect))
+
+
+def preprocess(scene: DeviceScene, camera, out: Projected | None = None, stream=None) -> Projected:
+    lib = load()
+    if out is None:
+        out = Projected.empty(scene.n, scene.means.device)
+    s, c, o = scene.struct(), camera_struct(camera), out.struct()
+    _check(lib.tgs_preprocess(C.byref(s), C.byref(c), C.byref(o), _stream(stream)))
+    return out
+
+
+# ------------------------------------------------------------------------------------------------
+# tgs_bin_sort
+
+@dataclass
+class Bins:
+    capacity: int
+    tiling: tuple
+    keys: "object"         # [capacity] int64 storage of uint64 keys
+    vals: "object"         # [capacity] int32 storage of uint32 indices
+    masks: "object"        # [capacity] int16 storage of uint16 masks
+    ranges: "object"       # [G,2] int32 storage of uint32
+    num_entries: "object"  # [1] int64 (device)
+    workspace: "object"    # uint8 workspace
+    entries: int = -1      # host copy of the count when known
+
+    def struct(self) -> _Bins:
+        return _Bins(self.capacity, _ptr(self.keys), _ptr(self.vals), _ptr(self.masks), _ptr(self.ranges),
+                     _ptr(self.num_entries))
+
+
+def workspace_size(n, capacity, width, height, tiling) -> int:
+    lib = load()
+    out = C.c_size_t(0)
+    t = _tiling(tiling)
+    _check(lib.tgs_bin_sort_workspace_size(int(n), int(capacity), int(width), int(height), C.byref(t),
+                                           C.byref(out)))
+    return int(out.value)
+
+
+def allocate_bins(n, capacity, width, height, tiling, device="cuda", keys=True) -> Bins:
+    GX, GY = group_grid(width, height, tiling)
+    ws = workspace_size(n, capacity, width, height, tiling)
+    cap = max(int(capacity), 1)
+    return Bins(int(capacity), tuple(tiling),
+                torch.empty(cap, dtype=torch.int64, device=device) if keys else None,
+                torch.empty(cap, dtype=torch.int32, device=device),
+                torch.empty(cap, dtype=torch.int16, device=device),
+                torch.empty((GX * GY, 2), dtype=torch.int32, device=device),
+                torch.zeros(1, dtype=torch.int64, device=device),
+                torch.empty(max(ws, 256), dtype=torch.uint8, device=device))
+
+
+def bin_sort(proj: Projected, width, height, tiling=(2, 2), bins: Bins | None = None, capacity=None,
+             sync=True, stream=None) -> Bins:
+    """Bins and sorts. With sync=True the entry count is read back (one stream sync) and the
+    capacity grows as needed; with sync=False the call is fully asynchronous and overflow leaves
+    every range empty (check bins.num_entries)."""
+    lib = load()
+    n = proj.n
+    if bins is None:
+        bins = allocate_bins(n, capacity if capacity is not None else max(1024, 8 * n), width, height,
+                             tiling, proj.mean2d.device)
+    t = _tiling(tiling)
+    while True:
+        b = bins.struct()
+        host = C.c_int64(0)
+        st = lib.tgs_bin_sort(C.byref(proj.struct()), n, int(width), int(height), C.byref(t),
+                              _ptr(bins.workspace), bins.workspace.numel(), C.byref(b),
+                              C.byref(host) if sync else None, _stream(stream))
+        if sync and st == TGS_ERR_CAPACITY:
+            bins = allocate_bins(n, int(host.value * 1.25) + 1024, width, height, tiling,
+                                 proj.mean2d.device, keys=bins.keys is not None)
+            continue
+        _check(st)
+        if sync:
+            bins.entries = int(host.value)
+        return bins
+
+
+# ------------------------------------------------------------------------------------------------
+# tgs_rasterize / tgs_rasterize_backward
+
+def rasterize(proj: Projected, bins: Bins, width, height, precision="fp16_tc", bg=(0.0, 0.0, 0.0),
+              out=None, want_n_contrib=True, counters=None, stream=None):
+    """Returns (rgb [3,H,W], T [H,W], n_contrib [H,W] or None)."""
+    lib = load()
+    dev = proj.mean2d.device
+    if out is None:
+        rgb = torch.empty((3, height, width), dtype=torch.float32, device=dev)
+        T = torch.empty((height, width), dtype=torch.float32, device=dev)
+        nc = torch.empty((height, width), dtype=torch.int32, device=dev) if want_n_contrib else None
+    else:
+        rgb, T, nc = out
+    o = _RasterOpts(PRECISION[precision], (C.c_float * 3)(*[float(v) for v in bg]), _ptr(counters))
+    t = _tiling(bins.tiling)
+    _check(lib.tgs_rasterize(C.byref(proj.struct()), proj.n, C.byref(bins.struct()), int(width), int(height),
+                             C.byref(t), C.byref(o), _ptr(rgb), _ptr(T), _ptr(nc), _stream(stream)))
+    return rgb, T, nc
+
+
+def rasterize_backward(proj: Projected, bins: Bins, width, height, T, n_contrib, grad_rgb,
+                       bg=(0.0, 0.0, 0.0), stream=None):
+    """Returns (g_mean2d [n,2], g_conic_opacity [n,4], g_rgb [n,3])."""
+    lib = load()
+    n, dev = proj.n, proj.mean2d.device
+    gm = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    gco = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    gc = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    o = _RasterOpts(PRECISION["fp32"], (C.c_float * 3)(*[float(v) for v in bg]), None)
+    t = _tiling(bins.tiling)
+    g = grad_rgb.contiguous()
+    _check(lib.tgs_rasterize_backward(C.byref(proj.struct()), n, C.byref(bins.struct()), int(width),
+                                      int(height), C.byref(t), C.byref(o), _ptr(T), _ptr(n_contrib), _ptr(g),
+                                      _ptr(gm), _ptr(gco), _ptr(gc), _stream(stream)))
+    return gm, gco, gc
+
+
+def kernel_launch_count() -> int:
+    return int(load().tgs_kernel_launch_count())
+
+
+def last_device_error(reset=False) -> int:
+    return int(load().tgs_last_device_error(1 if reset else 0))
+
+
+def render(scene: DeviceScene, camera, tiling=(2, 2), precision="fp16_tc", bg=(0.0, 0.0, 0.0),
+           bins: Bins | None = None, sync=True, stream=None):
+    """preprocess -> bin_sort -> rasterize. Returns (rgb, T, n_contrib, proj, bins)."""
+    proj = preprocess(scene, camera, stream=stream)
+    bins = bin_sort(proj, camera.width, camera.height, tiling, bins=bins, sync=sync, stream=stream)
+    rgb, T, nc = rasterize(proj, bins, camera.width, camera.height, precision, bg, stream=stream)
+    return rgb, T, nc, proj, bins
+
+
+class RasterizeFn(torch.autograd.Function):
+    """Differentiable FP32 rasterization of projected Gaussians.
+
+    apply(mean2d [n,2], conic_opacity [n,4], rgb [n,3], depth, radius, rect, bins, width, height, bg)
+    -> image [3,H,W]. Backward gives gradients for mean2d, conic_opacity (a, b, c, opacity) and rgb.
+    The bins must have been built from the same projected Gaussians."""
+
+    @staticmethod
+    def forward(ctx, mean2d, conic_opacity, rgb, depth, radius, rect, bins, width, height, bg):
+        proj = Projected(mean2d.shape[0], mean2d.contiguous(), conic_opacity.contiguous(),
+                         rgb.contiguous(), depth, radius, rect)
+        img, T, nc = rasterize(proj, bins, width, height, "fp32", bg)
+        ctx.save_for_backward(proj.mean2d, proj.conic_opacity, proj.rgb, T, nc)
+        ctx.meta = (bins, width, height, bg, depth, radius, rect)
+        return img
+
+    @staticmethod
+    def backward(ctx, grad_img):
+        mean2d, co, rgb, T, nc = ctx.saved_tensors
+        bins, width, height, bg, depth, radius, rect = ctx.meta
+        proj = Projected(mean2d.shape[0], mean2d, co, rgb, depth, radius, rect)
+        gm, gco, gc = rasterize_backward(proj, bins, width, height, T, nc, grad_img, bg)
+        return gm, gco, gc, None, None, None, None, None, None, None

@@ -1,0 +1,237 @@
+// C-ABI entry points of the tgs library: argument validation, error reporting and dispatch to the
+// kernel launchers. Every public function is declared in include/tgs.h.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "tgs_internal.cuh"
+
+namespace tgs {
+
+static thread_local char g_msg[512] = "";
+static std::atomic<int64_t> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+  va_end(ap);
+}
+
+tgs_status cuda_status(cudaError_t e, const char* what) {
+  set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  return TGS_ERR_CUDA;
+}
+
+// One zero-initialized int32 per device, allocated on first use and kept for the process.
+int32_t* device_error_word() {
+  static std::mutex mu;
+  static int32_t* words[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!words[dev]) {
+    int32_t* p = nullptr;
+    if (cudaMalloc(&p, sizeof(int32_t)) != cudaSuccess) return nullptr;
+    if (cudaMemset(p, 0, sizeof(int32_t)) != cudaSuccess) return nullptr;
+    words[dev] = p;
+  }
+  return words[dev];
+}
+
+static bool valid_tiling(const tgs_tiling* t) {
+  return t && t->group_w >= 1 && t->group_w <= TGS_MAX_GROUP && t->group_h >= 1 &&
+         t->group_h <= TGS_MAX_GROUP;
+}
+
+static bool valid_size(int32_t w, int32_t h) { return w >= 1 && h >= 1 && w <= 16384 && h <= 16384; }
+
+static int num_groups(int32_t w, int32_t h, const tgs_tiling* t) {
+  const int tx = div_up(w, kTile), ty = div_up(h, kTile);
+  return div_up(tx, t->group_w) * div_up(ty, t->group_h);
+}
+
+static tgs_status require_sm103(int32_t device) {
+  cudaDeviceProp prop;
+  TGS_CUDA(cudaGetDeviceProperties(&prop, device));
+  if (prop.major != 10 || prop.minor != 3) {
+    set_error("device %d is sm_%d%d; this library is built for sm_103a", device, prop.major,
+              prop.minor);
+    return TGS_ERR_UNSUPPORTED_DEVICE;
+  }
+  return TGS_OK;
+}
+
+static tgs_status require_current_sm103() {
+  int dev = 0;
+  TGS_CUDA(cudaGetDevice(&dev));
+  static int cached[64] = {0};  // 0 unknown, 1 ok, 2 unsupported
+  if (dev >= 0 && dev < 64 && cached[dev] == 1) return TGS_OK;
+  tgs_status s = require_sm103(dev);
+  if (dev >= 0 && dev < 64) cached[dev] = (s == TGS_OK) ? 1 : 2;
+  return s;
+}
+
+}  // namespace tgs
+
+using namespace tgs;
+
+extern "C" {
+
+const char* tgs_status_string(tgs_status s) {
+  switch (s) {
+    case TGS_OK: return "TGS_OK";
+    case TGS_ERR_INVALID_ARGUMENT: return "TGS_ERR_INVALID_ARGUMENT";
+    case TGS_ERR_CUDA: return "TGS_ERR_CUDA";
+    case TGS_ERR_CAPACITY: return "TGS_ERR_CAPACITY";
+    case TGS_ERR_UNSUPPORTED_DEVICE: return "TGS_ERR_UNSUPPORTED_DEVICE";
+    case TGS_ERR_TIMEOUT: return "TGS_ERR_TIMEOUT";
+    case TGS_ERR_BUSY: return "TGS_ERR_BUSY";
+    case TGS_ERR_NOT_FOUND: return "TGS_ERR_NOT_FOUND";
+    default: return "TGS_ERR_UNKNOWN";
+  }
+}
+
+const char* tgs_last_error_message(void) { return g_msg; }
+
+int32_t tgs_abi_version(void) { return TGS_ABI_VERSION; }
+
+int64_t tgs_kernel_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+tgs_status tgs_check_device(int32_t device) { return require_sm103(device); }
+
+tgs_status tgs_preprocess(const tgs_scene* scene, const tgs_camera* cam, tgs_projected* out,
+                          void* stream) {
+  g_msg[0] = 0;
+  if (!scene || !cam || !out) return set_error("null argument"), TGS_ERR_INVALID_ARGUMENT;
+  if (scene->n < 0 || scene->n >= (int64_t(1) << 31))
+    return set_error("n = %lld out of range", (long long)scene->n), TGS_ERR_INVALID_ARGUMENT;
+  if (scene->sh_degree < 0 || scene->sh_degree > 3)
+    return set_error("sh_degree %d not in 0..3", scene->sh_degree), TGS_ERR_INVALID_ARGUMENT;
+  if (!valid_size(cam->width, cam->height) || !(cam->fx > 0) || !(cam->fy > 0))
+    return set_error("bad camera (size or focal length)"), TGS_ERR_INVALID_ARGUMENT;
+  if (scene->n == 0) return TGS_OK;
+  if (!scene->means || !scene->scales || !scene->quats || !scene->opacities || !scene->sh ||
+      !out->mean2d || !out->conic_opacity || !out->rgb || !out->depth || !out->radius || !out->rect)
+    return set_error("null array"), TGS_ERR_INVALID_ARGUMENT;
+  tgs_status s = require_current_sm103();
+  if (s != TGS_OK) return s;
+  return launch_preprocess(*scene, *cam, *out, (cudaStream_t)stream);
+}
+
+tgs_status tgs_bin_sort_workspace_size(int64_t n, int64_t capacity, int32_t width, int32_t height,
+                                       const tgs_tiling* tiling, size_t* bytes) {
+  g_msg[0] = 0;
+  if (!bytes || !valid_tiling(tiling) || !valid_size(width, height) || n < 0 || capacity < 0 ||
+      capacity >= (int64_t(1) << 32) || n >= (int64_t(1) << 31))
+    return set_error("bad argument"), TGS_ERR_INVALID_ARGUMENT;
+  *bytes = bin_sort_workspace_bytes(n, capacity, num_groups(width, height, tiling));
+  return TGS_OK;
+}
+
+tgs_status tgs_bin_sort(const tgs_projected* proj, int64_t n, int32_t width, int32_t height,
+                        const tgs_tiling* tiling, void* workspace, size_t workspace_bytes,
+                        tgs_bins* bins, int64_t* num_entries_host, void* stream) {
+  g_msg[0] = 0;
+  if (!proj || !bins || !valid_tiling(tiling) || !valid_size(width, height) || n < 0 ||
+      n >= (int64_t(1) << 31))
+    return set_error("bad argument"), TGS_ERR_INVALID_ARGUMENT;
+  if (bins->capacity < 0 || bins->capacity >= (int64_t(1) << 32))
+    return set_error("capacity out of range"), TGS_ERR_INVALID_ARGUMENT;
+  if (!bins->ranges || !bins->num_entries || (bins->capacity > 0 && (!bins->vals || !bins->masks)))
+    return set_error("null bins array"), TGS_ERR_INVALID_ARGUMENT;
+  if (n > 0 && (!proj->rect || !proj->depth || !proj->radius))
+    return set_error("null projected array"), TGS_ERR_INVALID_ARGUMENT;
+  const size_t need = bin_sort_workspace_bytes(n, bins->capacity, num_groups(width, height, tiling));
+  if (workspace_bytes < need || (need > 0 && !workspace) || ((uintptr_t)workspace & 255))
+    return set_error("workspace too small or misaligned: need %zu bytes", need),
+           TGS_ERR_INVALID_ARGUMENT;
+  tgs_status s = require_current_sm103();
+  if (s != TGS_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  s = launch_bin_sort(*proj, n, width, height, tiling->group_w, tiling->group_h, workspace,
+                      workspace_bytes, *bins, st);
+  if (s != TGS_OK || !num_entries_host) return s;
+  TGS_CUDA(cudaMemcpyAsync(num_entries_host, bins->num_entries, sizeof(int64_t),
+                           cudaMemcpyDeviceToHost, st));
+  TGS_CUDA(cudaStreamSynchronize(st));
+  if (*num_entries_host > bins->capacity) {
+    set_error("frame needs %lld entries, capacity %lld", (long long)*num_entries_host,
+              (long long)bins->capacity);
+    return TGS_ERR_CAPACITY;
+  }
+  return TGS_OK;
+}
+
+static tgs_status check_raster_args(const tgs_projected* proj, const tgs_bins* bins, int32_t width,
+                                    int32_t height, const tgs_tiling* tiling,
+                                    const tgs_raster_opts* opts) {
+  if (!proj || !bins || !opts || !valid_tiling(tiling) || !valid_size(width, height))
+    return set_error("bad argument"), TGS_ERR_INVALID_ARGUMENT;
+  if (!bins->ranges || (bins->capacity > 0 && (!bins->vals || !bins->masks)))
+    return set_error("null bins array"), TGS_ERR_INVALID_ARGUMENT;
+  if (!proj->mean2d || !proj->conic_opacity || !proj->rgb)
+    return set_error("null projected array"), TGS_ERR_INVALID_ARGUMENT;
+  return TGS_OK;
+}
+
+tgs_status tgs_rasterize(const tgs_projected* proj, int64_t n, const tgs_bins* bins, int32_t width,
+                         int32_t height, const tgs_tiling* tiling, const tgs_raster_opts* opts,
+                         float* out_rgb, float* out_T, int32_t* n_contrib, void* stream) {
+  g_msg[0] = 0;
+  (void)n;
+  tgs_status s = check_raster_args(proj, bins, width, height, tiling, opts);
+  if (s != TGS_OK) return s;
+  if (!out_rgb || !out_T) return set_error("null output"), TGS_ERR_INVALID_ARGUMENT;
+  s = require_current_sm103();
+  if (s != TGS_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (opts->precision) {
+    case TGS_PRECISION_FP32:
+      return launch_raster_fp32(*proj, *bins, width, height, tiling->group_w, tiling->group_h,
+                                *opts, out_rgb, out_T, n_contrib, st);
+    case TGS_PRECISION_FP16_TC:
+      return launch_raster_tc(*proj, *bins, width, height, tiling->group_w, tiling->group_h, *opts,
+                              out_rgb, out_T, n_contrib, st);
+    default:
+      set_error("unknown precision %d", opts->precision);
+      return TGS_ERR_INVALID_ARGUMENT;
+  }
+}
+
+tgs_status tgs_rasterize_backward(const tgs_projected* proj, int64_t n, const tgs_bins* bins,
+                                  int32_t width, int32_t height, const tgs_tiling* tiling,
+                                  const tgs_raster_opts* opts, const float* out_T,
+                                  const int32_t* n_contrib, const float* grad_rgb,
+                                  float* g_mean2d, float* g_conic_opacity, float* g_rgb,
+                                  void* stream) {
+  g_msg[0] = 0;
+  tgs_status s = check_raster_args(proj, bins, width, height, tiling, opts);
+  if (s != TGS_OK) return s;
+  if (n < 0 || n >= (int64_t(1) << 31)) return set_error("bad n"), TGS_ERR_INVALID_ARGUMENT;
+  if (!out_T || !n_contrib || !grad_rgb || (n > 0 && (!g_mean2d || !g_conic_opacity || !g_rgb)))
+    return set_error("null argument"), TGS_ERR_INVALID_ARGUMENT;
+  s = require_current_sm103();
+  if (s != TGS_OK) return s;
+  return launch_raster_backward(*proj, n, *bins, width, height, tiling->group_w, tiling->group_h,
+                                *opts, out_T, n_contrib, grad_rgb, g_mean2d, g_conic_opacity, g_rgb,
+                                (cudaStream_t)stream);
+}
+
+tgs_status tgs_last_device_error(int32_t reset) {
+  g_msg[0] = 0;
+  int32_t* w = device_error_word();
+  if (!w) return set_error("device error word unavailable"), TGS_ERR_CUDA;
+  TGS_CUDA(cudaDeviceSynchronize());
+  int32_t v = 0;
+  TGS_CUDA(cudaMemcpy(&v, w, sizeof v, cudaMemcpyDeviceToHost));
+  if (reset) TGS_CUDA(cudaMemset(w, 0, sizeof(int32_t)));
+  if (v != TGS_OK) set_error("a device pipeline wait expired (code %d)", v);
+  return v;
+}
+
+}  // extern "C"

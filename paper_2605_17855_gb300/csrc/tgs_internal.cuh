@@ -1,0 +1,219 @@
+// Internal helpers of the tgs library: error plumbing, PTX wrappers for mbarriers, tcgen05 tensor
+// memory and MMA on sm_103a, and small numeric helpers. Not part of the ABI.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tgs.h"
+
+namespace tgs {
+
+// ---------------------------------------------------------------------------------------------
+// Host-side error plumbing (implemented in abi.cu).
+void set_error(const char* fmt, ...);
+tgs_status cuda_status(cudaError_t e, const char* what);
+// Device-side error word of the current device (allocated once per device, zero-initialized).
+int32_t* device_error_word();
+
+#define TGS_CUDA(expr)                                              \
+  do {                                                              \
+    cudaError_t _e = (expr);                                        \
+    if (_e != cudaSuccess) return ::tgs::cuda_status(_e, #expr);    \
+  } while (0)
+
+void note_launch();  // counts kernel launches (tgs_kernel_launch_count)
+
+#define TGS_CHECK_LAUNCH(what)                                      \
+  do {                                                              \
+    ::tgs::note_launch();                                           \
+    cudaError_t _e = cudaGetLastError();                            \
+    if (_e != cudaSuccess) return ::tgs::cuda_status(_e, what);     \
+  } while (0)
+
+constexpr int kTile = TGS_TILE;
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Launchers implemented by the kernel translation units.
+tgs_status launch_preprocess(const tgs_scene& s, const tgs_camera& cam, const tgs_projected& out,
+                             cudaStream_t st);
+size_t bin_sort_workspace_bytes(int64_t n, int64_t capacity, int num_groups);
+tgs_status launch_bin_sort(const tgs_projected& p, int64_t n, int width, int height, int gw, int gh,
+                           void* ws, size_t ws_bytes, const tgs_bins& bins, cudaStream_t st);
+tgs_status launch_raster_fp32(const tgs_projected& p, const tgs_bins& b, int width, int height,
+                              int gw, int gh, const tgs_raster_opts& o, float* out_rgb, float* out_T,
+                              int32_t* n_contrib, cudaStream_t st);
+tgs_status launch_raster_tc(const tgs_projected& p, const tgs_bins& b, int width, int height, int gw,
+                            int gh, const tgs_raster_opts& o, float* out_rgb, float* out_T,
+                            int32_t* n_contrib, cudaStream_t st);
+tgs_status launch_raster_backward(const tgs_projected& p, int64_t n, const tgs_bins& b, int width,
+                                  int height, int gw, int gh, const tgs_raster_opts& o,
+                                  const float* out_T, const int32_t* n_contrib, const float* grad_rgb,
+                                  float* g_mean2d, float* g_conic_opacity, float* g_rgb,
+                                  cudaStream_t st);
+
+// ---------------------------------------------------------------------------------------------
+// Device helpers.
+
+// Blend constants of Section 2 (pruning threshold, clamp, termination threshold).
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Hardware base-2 exponential (PTX ex2.approx.ftz.f32).
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// Hardware base-2 logarithm (PTX lg2.approx.ftz.f32).
+__device__ __forceinline__ float lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Power of Eq. tensorgs_power_scalar, -1/2 (a dx^2 + c dy^2) - b dx dy, with a fixed operation
+// order (no contraction choices left to the compiler), clamped at 0 (a positive value can only come
+// from rounding). The FP32 forward, the backward replay and the scalar fallback of the tensor path
+// all call this, so their decisions agree bit for bit.
+__device__ __forceinline__ float power_fp32(float a, float b, float c, float dx, float dy) {
+  const float s = __fmaf_rn(__fmul_rn(a, dx), dx, __fmul_rn(__fmul_rn(c, dy), dy));
+  const float p = __fmaf_rn(-0.5f, s, -__fmul_rn(__fmul_rn(b, dx), dy));
+  return fminf(p, 0.f);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ---- mbarrier -----------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after `limit_ns` (or when *abort is set) and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  volatile int* abort, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbarrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// ---- tcgen05: tensor memory ---------------------------------------------------------------
+// Allocation is done by one whole warp; the TMEM address is written to shared memory.
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_addr(dst_smem)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor for tcgen05.mma, no swizzle, K-major canonical layout:
+// core matrices of 8 rows x 16 bytes (rows 16 B apart); `lbo` = byte distance between the two core
+// matrices adjacent along K, `sbo` = byte distance between 8-row groups along M/N.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  // base offset 0, absolute LBO mode 0, layout type 0 (no swizzle)
+  return d;
+}
+
+// Instruction descriptor of tcgen05.mma.kind::f16 with FP32 accumulation, both operands K-major.
+// ab_bf16 selects BF16 (else FP16) for A and B.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool ab_bf16) {
+  return (1u << 4)                              // D format: F32
+         | ((ab_bf16 ? 1u : 0u) << 7)           // A format
+         | ((ab_bf16 ? 1u : 0u) << 10)          // B format
+         | ((uint32_t)(N >> 3) << 17)           // N / 8
+         | ((uint32_t)(M >> 4) << 24);          // M / 16
+}
+
+// D[tmem] (=|+=) A[smem] * B[smem]^T, issued by a single thread.
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                        uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive on `bar` once all tcgen05 operations previously issued by this thread complete.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+
+// Two tensor-memory loads (shape 32x32b, 16 consecutive 32-bit columns each) followed by the
+// wait, in one asm statement so that no use of the results can be scheduled before the wait.
+// Lane of the warp = TMEM lane (32 * (warp % 4) + laneid); taddr selects lane base and column.
+__device__ __forceinline__ void tmem_ld_2x16(uint32_t ta, uint32_t tb, float (&a)[16],
+                                             float (&b)[16]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%33];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]),"=r"(r[1]),"=r"(r[2]),"=r"(r[3]),"=r"(r[4]),"=r"(r[5]),"=r"(r[6]),"=r"(r[7]),"=r"(r[8]),"=r"(r[9]),"=r"(r[10]),"=r"(r[11]),"=r"(r[12]),"=r"(r[13]),"=r"(r[14]),"=r"(r[15]),"=r"(r[16]),"=r"(r[17]),"=r"(r[18]),"=r"(r[19]),"=r"(r[20]),"=r"(r[21]),"=r"(r[22]),"=r"(r[23]),"=r"(r[24]),"=r"(r[25]),"=r"(r[26]),"=r"(r[27]),"=r"(r[28]),"=r"(r[29]),"=r"(r[30]),"=r"(r[31])
+      : "r"(ta), "r"(tb)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    a[i] = __uint_as_float(r[i]);
+    b[i] = __uint_as_float(r[16 + i]);
+  }
+}
+
+}  // namespace tgs

@@ -1,0 +1,109 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports every function that
+include/*.h declares, validates arguments before touching the device, and the product package is
+independent of the oracle."""
+import ast
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(tgs_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2605_17855_gb300 as tgs
+    return tgs.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("tgs_preprocess", "tgs_bin_sort", "tgs_rasterize", "tgs_rasterize_backward"):
+        assert required in names
+
+
+def test_library_exports_every_declared_function(lib):
+    import paper_2605_17855_gb300 as tgs
+    names = _declared_functions()
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert names <= set(tgs.SIGNATURES), names - set(tgs.SIGNATURES)
+
+
+def test_status_strings_and_version(lib):
+    assert lib.tgs_abi_version() == 1
+    assert lib.tgs_status_string(0) == b"TGS_OK"
+    assert lib.tgs_status_string(3) == b"TGS_ERR_CAPACITY"
+    assert lib.tgs_status_string(99) == b"TGS_ERR_UNKNOWN"
+
+
+def test_argument_validation_is_host_side(lib):
+    import ctypes as C
+
+    import paper_2605_17855_gb300 as tgs
+    out = C.c_size_t(0)
+    bad = tgs._Tiling(0, 2)
+    assert lib.tgs_bin_sort_workspace_size(10, 10, 64, 64, C.byref(bad), C.byref(out)) == 1
+    good = tgs._Tiling(2, 2)
+    assert lib.tgs_bin_sort_workspace_size(10, 10, 64, 64, C.byref(good), C.byref(out)) == 0
+    assert out.value > 0
+    assert lib.tgs_bin_sort_workspace_size(10, 10, 0, 64, C.byref(good), C.byref(out)) == 1
+    # preprocess: bad SH degree and bad camera are rejected before any device work
+    s = tgs._Scene(5, 7, None, None, None, None, None)
+    cam = tgs._Camera()
+    cam.width, cam.height, cam.fx, cam.fy = 64, 64, 50.0, 50.0
+    proj = tgs._Projected()
+    assert lib.tgs_preprocess(C.byref(s), C.byref(cam), C.byref(proj), None) == 1
+    assert b"sh_degree" in lib.tgs_last_error_message()
+    s = tgs._Scene(0, 0, None, None, None, None, None)
+    assert lib.tgs_preprocess(C.byref(s), C.byref(cam), C.byref(proj), None) == 0  # empty scene: no-op
+    cam.fx = -1.0
+    assert lib.tgs_preprocess(C.byref(s), C.byref(cam), C.byref(proj), None) == 1
+    # rasterize: null options
+    b = tgs._Bins()
+    assert lib.tgs_rasterize(C.byref(proj), 0, C.byref(b), 64, 64, C.byref(good), None, None, None, None,
+                             None) == 1
+
+
+def test_workspace_grows_with_capacity(lib):
+    import paper_2605_17855_gb300 as tgs
+    a = tgs.workspace_size(1000, 1000, 128, 128, (2, 2))
+    b = tgs.workspace_size(1000, 100000, 128, 128, (2, 2))
+    assert b > a
+
+
+def _imports(path):
+    tree = ast.parse(open(path).read())
+    mods = set()
+    for node in ast.walk(tree):
+        if isinstance(node, ast.Import):
+            mods |= {a.name.split(".")[0] for a in node.names}
+        elif isinstance(node, ast.ImportFrom) and node.module:
+            mods.add(node.module.split(".")[0])
+    return mods
+
+
+def test_product_never_imports_the_oracle():
+    for p in glob.glob(os.path.join(ROOT, "paper_2605_17855_gb300", "**", "*.py"), recursive=True):
+        assert "oracle" not in _imports(p), p
+    for p in glob.glob(os.path.join(ROOT, "paper_2605_17855_gb300", "csrc", "*")):
+        assert "oracle" not in open(p).read().lower(), p
+
+
+def test_oracle_never_imports_the_product():
+    for p in glob.glob(os.path.join(ROOT, "oracle", "*.py")):
+        assert "paper_2605_17855_gb300" not in _imports(p), p
+    for p in glob.glob(os.path.join(ROOT, "oracle", "*.[ch]")):
+        assert "tgs_internal" not in open(p).read() and "tgs.h" not in open(p).read()

@@ -1,0 +1,369 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Bars (from the method's statement of exactness and the stated tolerances):
+  * binning and sort: bit-exact keys, indices, masks, ranges and counts, given the same projected
+    Gaussians;
+  * FP32 CUDA-core rasterizer: max abs <= 1e-4 on every pixel whose threshold decisions are not
+    within 1e-5 (relative) of a threshold; T and n_contrib equal there too;
+  * FP16 tensor-core rasterizer: PSNR >= 45 dB over all pixels and max abs <= 2/255 on pixels
+    whose decisions are not within 1e-3 of a threshold;
+  * backward: relative L2 error <= 1e-3 per gradient tensor against the oracle's analytic gradient.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU-only hosts
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_2605_17855_gb300 as tgs  # noqa: E402
+from paper_2605_17855_gb300 import scenes  # noqa: E402
+
+FP32_TOL = 1e-4
+TC_MAXABS = 2.0 / 255.0
+TC_PSNR = 45.0
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _proj_np(proj):
+    co = _np(proj.conic_opacity).astype(np.float64)
+    return dict(mean2d=_np(proj.mean2d).astype(np.float64), conic=co[:, :3], opacity=co[:, 3],
+                rgb=_np(proj.rgb).astype(np.float64), depth=_np(proj.depth), radius=_np(proj.radius),
+                rect=_np(proj.rect))
+
+
+def _gpu_frame(scene, cam, tiling=(2, 2)):
+    ds = tgs.DeviceScene.from_host(scene)
+    proj = tgs.preprocess(ds, cam)
+    bins = tgs.bin_sort(proj, cam.width, cam.height, tiling)
+    return ds, proj, bins
+
+
+def _oracle_bins(p, cam, tiling):
+    return oracle.bin_sort(p["mean2d"], p["radius"], p["depth"], cam.width, cam.height, *tiling)
+
+
+def _oracle_image(p, cam, ob, pixels=None):
+    return oracle.blend(cam.width, cam.height, p["mean2d"], p["conic"], p["opacity"], p["rgb"], ob,
+                        pixels=pixels)
+
+
+def _chw(img_hwc):
+    return img_hwc.transpose(2, 0, 1)
+
+
+# ------------------------------------------------------------------------------------------------
+# Workloads: the 2,000-splat 128x128 scene, a ragged image (not a multiple of 16, groups cut at the
+# border, splats off screen and behind the camera), and an SH-degree-3 mixture scene.
+
+def _ragged():
+    scene = scenes.box_scene(3000, seed=21, sh_degree=1, log_scale_mean=-3.2)
+    scene.means[:50, 2] = -1.0          # behind the camera
+    scene.means[50:100, 0] *= 3.0       # far off the side
+    cam = scenes.identity_camera(203, 117, 70.0)
+    return scene, cam
+
+
+def _mixture_small():
+    scene = scenes.mixture_scene(40_000, seed=31, components=32, cluster_std=0.3, radius=2.0,
+                                 log_scale_mean=-3.8, sh_degree=3, needle_fraction=0.05)
+    cam = scenes.orbit_cameras(8, 5.0, 320, 240)[3]
+    return scene, cam
+
+
+CASES = {
+    "c1": lambda: (lambda s, c: (s, c[0]))(*scenes.config_c1()),
+    "ragged": _ragged,
+    "mixture": _mixture_small,
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    scene, cam = CASES[request.param]()
+    return request.param, scene, cam
+
+
+# ------------------------------------------------------------------------------------------------
+# R1 preprocess
+
+def test_preprocess_matches_oracle(case):
+    name, scene, cam = case
+    _, proj, _ = _gpu_frame(scene, cam)
+    torch.cuda.synchronize()
+    p = _proj_np(proj)
+    o = oracle.preprocess(scene, cam)
+    vis_g, vis_o = p["radius"] > 0, o.radius > 0
+    both = vis_g & vis_o
+    # visibility and radius can flip only where ceil(3 sqrt(lambda)) or the AABB sits on an integer
+    assert (vis_g != vis_o).sum() <= max(2, 1e-3 * scene.n)
+    assert (p["radius"][both] != o.radius[both]).sum() <= max(2, 1e-3 * scene.n)
+    np.testing.assert_allclose(p["mean2d"][both], o.mean2d[both], rtol=1e-6, atol=1e-4)
+    np.testing.assert_allclose(p["depth"][both], o.depth[both], rtol=1e-6)
+    np.testing.assert_allclose(p["opacity"][both], o.opacity[both], rtol=0, atol=0)
+    np.testing.assert_allclose(p["rgb"][both], o.rgb[both], rtol=1e-5, atol=1e-5)
+    # conic: relative to its largest entry (the FP64 branch keeps near-degenerate ones accurate)
+    scale = np.abs(o.conic[both]).max(axis=1, keepdims=True)
+    err = np.abs(p["conic"][both] - o.conic[both]) / scale
+    assert err.max() < 2e-5, err.max()
+    same_r = both & (p["radius"] == o.radius)
+    assert (p["rect"][same_r] != o.rect[same_r]).any(axis=1).sum() <= max(2, 1e-3 * scene.n)
+
+
+# ------------------------------------------------------------------------------------------------
+# R2 bin + group + sort: bit-exact given the same projected Gaussians
+
+@pytest.mark.parametrize("tiling", [(1, 1), (2, 2), (4, 2), (4, 4), (3, 1)])
+def test_bin_sort_bit_exact(case, tiling):
+    name, scene, cam = case
+    _, proj, bins = _gpu_frame(scene, cam, tiling)
+    torch.cuda.synchronize()
+    p = _proj_np(proj)
+    ob = _oracle_bins(p, cam, tiling)
+    E = bins.entries
+    assert E == ob.num_entries
+    assert np.array_equal(_np(bins.keys[:E]).view(np.uint64), ob.keys)
+    assert np.array_equal(_np(bins.vals[:E]).view(np.uint32), ob.vals)
+    assert np.array_equal(_np(bins.masks[:E]).view(np.uint16), ob.masks)
+    assert np.array_equal(_np(bins.ranges).view(np.uint32), ob.ranges)
+    assert int(_np(bins.num_entries)[0]) == E
+
+
+def test_bin_sort_capacity_overflow():
+    scene, cams = scenes.config_c1()
+    cam = cams[0]
+    ds = tgs.DeviceScene.from_host(scene)
+    proj = tgs.preprocess(ds, cam)
+    small = tgs.allocate_bins(scene.n, 100, cam.width, cam.height, (2, 2))
+    # asynchronous call: overflow leaves every range empty and reports the needed count
+    tgs.bin_sort(proj, cam.width, cam.height, (2, 2), bins=small, sync=False)
+    torch.cuda.synchronize()
+    need = int(_np(small.num_entries)[0])
+    assert need > 100
+    assert not _np(small.ranges).any()
+    # synchronous call through the raw ABI returns TGS_ERR_CAPACITY
+    import ctypes as C
+    lib = tgs.load()
+    host = C.c_int64(0)
+    t = tgs._Tiling(2, 2)
+    st = lib.tgs_bin_sort(C.byref(proj.struct()), scene.n, cam.width, cam.height, C.byref(t),
+                          small.workspace.data_ptr(), small.workspace.numel(), C.byref(small.struct()),
+                          C.byref(host), None)
+    assert st == tgs.TGS_ERR_CAPACITY and host.value == need
+    # the binding grows the capacity and retries
+    grown = tgs.bin_sort(proj, cam.width, cam.height, (2, 2), bins=small)
+    assert grown.entries == need
+
+
+# ------------------------------------------------------------------------------------------------
+# R4/R5 rasterize
+
+def _raster_vs_oracle(scene, cam, tiling, precision, counters=False):
+    _, proj, bins = _gpu_frame(scene, cam, tiling)
+    cnt = torch.zeros(2, dtype=torch.int64, device="cuda") if counters else None
+    rgb, T, nc = tgs.rasterize(proj, bins, cam.width, cam.height, precision, counters=cnt)
+    torch.cuda.synchronize()
+    assert tgs.last_device_error() == 0
+    p = _proj_np(proj)
+    ob = _oracle_bins(p, cam, tiling)
+    img = _oracle_image(p, cam, ob)
+    return (_np(rgb), _np(T), _np(nc), img, (int(_np(cnt)[0]) if counters else None))
+
+
+@pytest.mark.parametrize("tiling", [(1, 1), (2, 2), (4, 2)])
+def test_fp32_raster_parity(case, tiling):
+    name, scene, cam = case
+    rgb, T, nc, img, ev = _raster_vs_oracle(scene, cam, tiling, "fp32", counters=True)
+    ok = img.margin > 1e-5
+    assert (~ok).mean() < 1e-3
+    err = np.abs(rgb - _chw(img.rgb)).max(axis=0)
+    assert err[ok].max() <= FP32_TOL, err[ok].max()
+    assert np.abs(T - img.T)[ok].max() <= FP32_TOL
+    assert np.array_equal(nc[ok], img.n_contrib[ok])
+    # evaluated (pixel, entry) pairs: equal to the oracle's count up to ambiguous pixels
+    assert abs(ev - img.evaluated) <= 0.001 * img.evaluated + 10
+
+
+@pytest.mark.parametrize("tiling", [(1, 1), (2, 2), (4, 2), (2, 4), (4, 4)])
+def test_tc_raster_parity(case, tiling):
+    name, scene, cam = case
+    rgb, T, nc, img, ev = _raster_vs_oracle(scene, cam, tiling, "fp16_tc", counters=True)
+    ref = _chw(img.rgb)
+    psnr = oracle.psnr(rgb, ref)
+    assert psnr >= TC_PSNR, psnr
+    ok = img.margin > 1e-3
+    assert (~ok).mean() < 0.01
+    err = np.abs(rgb - ref).max(axis=0)
+    assert err[ok].max() <= TC_MAXABS, err[ok].max()
+    assert abs(ev - img.evaluated) <= 0.01 * img.evaluated + 10
+
+
+def test_grouping_is_exact_on_gpu(case):
+    # Section 4.4.2: grouped rasterization is numerically equivalent to per-tile rasterization.
+    # Both paths use per-tile arithmetic, so the images are bit-identical.
+    name, scene, cam = case
+    outs = {}
+    for tiling in [(1, 1), (2, 2), (4, 2)]:
+        _, proj, bins = _gpu_frame(scene, cam, tiling)
+        for prec in ("fp32", "fp16_tc"):
+            rgb, T, _ = tgs.rasterize(proj, bins, cam.width, cam.height, prec, want_n_contrib=False)
+            outs[(tiling, prec)] = (_np(rgb), _np(T))
+    for prec in ("fp32", "fp16_tc"):
+        base = outs[((1, 1), prec)]
+        for tiling in [(2, 2), (4, 2)]:
+            assert np.array_equal(outs[(tiling, prec)][0], base[0]), (tiling, prec)
+            assert np.array_equal(outs[(tiling, prec)][1], base[1]), (tiling, prec)
+
+
+def test_background_and_empty_inputs():
+    cam = scenes.identity_camera(70, 33)
+    bg = (0.25, 0.5, 1.0)
+    # empty scene
+    empty = scenes.box_scene(0, seed=1)
+    for prec in ("fp32", "fp16_tc"):
+        _, proj, bins = _gpu_frame(empty, cam)
+        assert bins.entries == 0
+        rgb, T, nc = tgs.rasterize(proj, bins, cam.width, cam.height, prec, bg=bg)
+        torch.cuda.synchronize()
+        assert np.all(_np(T) == 1.0) and np.all(_np(nc) == 0)
+        for c in range(3):
+            assert np.all(_np(rgb)[c] == np.float32(bg[c]))
+    # every splat culled (behind the camera)
+    s = scenes.box_scene(500, seed=2)
+    s.means[:, 2] = -3.0
+    _, proj, bins = _gpu_frame(s, cam)
+    assert bins.entries == 0 and int(_np(proj.radius).max()) == 0
+
+
+def test_background_blend():
+    scene, cams = scenes.config_c1()
+    cam = cams[0]
+    bg = (0.2, 0.4, 0.6)
+    _, proj, bins = _gpu_frame(scene, cam)
+    p = _proj_np(proj)
+    img = oracle.blend(cam.width, cam.height, p["mean2d"], p["conic"], p["opacity"], p["rgb"],
+                       _oracle_bins(p, cam, (2, 2)), bg=bg)
+    ok = img.margin > 1e-5
+    rgb, _, _ = tgs.rasterize(proj, bins, cam.width, cam.height, "fp32", bg=bg)
+    assert np.abs(_np(rgb) - _chw(img.rgb)).max(axis=0)[ok].max() <= FP32_TOL
+    rgb, _, _ = tgs.rasterize(proj, bins, cam.width, cam.height, "fp16_tc", bg=bg)
+    assert oracle.psnr(_np(rgb), _chw(img.rgb)) >= TC_PSNR
+
+
+def test_tc_scalar_fallback_rows():
+    # thin, large splats far from their tiles' centres exercise the scalar FP32 rows of the
+    # tensor-core path; the image still meets the tolerance
+    scene = scenes.mixture_scene(3000, seed=41, components=4, cluster_std=0.2, radius=0.8,
+                                 log_scale_mean=-2.5, log_scale_std=0.3, sh_degree=0,
+                                 needle_fraction=0.5, needle_ratio=400.0)
+    cam = scenes.orbit_cameras(4, 3.0, 256, 192)[1]
+    rgb, T, nc, img, _ = _raster_vs_oracle(scene, cam, (2, 2), "fp16_tc")
+    assert oracle.psnr(rgb, _chw(img.rgb)) >= TC_PSNR
+    ok = img.margin > 1e-3
+    assert np.abs(rgb - _chw(img.rgb)).max(axis=0)[ok].max() <= TC_MAXABS
+
+
+# ------------------------------------------------------------------------------------------------
+# Full-size workload (1.5M splats, 1600x1064, the launch configuration the benchmark times):
+# binning bit-exact over the whole frame, images checked on sampled tile groups.
+
+@pytest.fixture(scope="module")
+def c2_frame():
+    scene, cams = scenes.config_c2()
+    cam = cams[0]
+    ds, proj, bins = _gpu_frame(scene, cam, (2, 2))
+    torch.cuda.synchronize()
+    return scene, cam, proj, bins
+
+
+@pytest.mark.slow
+def test_c2_full_size_bins_bit_exact(c2_frame):
+    scene, cam, proj, bins = c2_frame
+    p = _proj_np(proj)
+    ob = _oracle_bins(p, cam, (2, 2))
+    E = bins.entries
+    assert E == ob.num_entries and E > 1_000_000
+    assert np.array_equal(_np(bins.keys[:E]).view(np.uint64), ob.keys)
+    assert np.array_equal(_np(bins.vals[:E]).view(np.uint32), ob.vals)
+    assert np.array_equal(_np(bins.masks[:E]).view(np.uint16), ob.masks)
+    assert np.array_equal(_np(bins.ranges).view(np.uint32), ob.ranges)
+
+
+@pytest.mark.slow
+def test_c2_full_size_sampled_pixels(c2_frame):
+    scene, cam, proj, bins = c2_frame
+    p = _proj_np(proj)
+    ob = _oracle_bins(p, cam, (2, 2))
+    rng = np.random.default_rng(0)
+    GX, GY = tgs.group_grid(cam.width, cam.height, (2, 2))
+    lens = ob.ranges[:, 1].astype(np.int64) - ob.ranges[:, 0]
+    busy = np.argsort(-lens)[:16]  # the longest lists
+    groups = np.unique(np.concatenate([busy, rng.choice(GX * GY, 48, replace=False)]))
+    pix = []
+    for g in groups:
+        gx, gy = g % GX, g // GX
+        for _ in range(64):
+            x = gx * 32 + int(rng.integers(0, 32))
+            y = gy * 32 + int(rng.integers(0, 32))
+            if x < cam.width and y < cam.height:
+                pix.append((x, y))
+    pix = np.array(pix)
+    img = _oracle_image(p, cam, ob, pixels=pix)
+    ref = img.rgb
+    for prec, tol, mtol in (("fp32", FP32_TOL, 1e-5), ("fp16_tc", TC_MAXABS, 1e-3)):
+        rgb, T, nc = tgs.rasterize(proj, bins, cam.width, cam.height, prec)
+        got = _np(rgb)[:, pix[:, 1], pix[:, 0]].T
+        ok = img.margin > mtol
+        assert np.abs(got - ref).max(axis=1)[ok].max() <= tol, prec
+        if prec == "fp16_tc":
+            assert oracle.psnr(got, ref) >= TC_PSNR
+
+
+# ------------------------------------------------------------------------------------------------
+# Backward (FP32): against the oracle's analytic gradient on the same projected inputs
+
+@pytest.mark.parametrize("tiling", [(1, 1), (2, 2)])
+def test_backward_matches_oracle(tiling):
+    scene, cams = scenes.config_c1()
+    cam = cams[0]
+    _, proj, bins = _gpu_frame(scene, cam, tiling)
+    rgb, T, nc = tgs.rasterize(proj, bins, cam.width, cam.height, "fp32")
+    rng = np.random.default_rng(3)
+    G = rng.standard_normal((3, cam.height, cam.width)).astype(np.float32)
+    gm, gco, gc = tgs.rasterize_backward(proj, bins, cam.width, cam.height, T, nc,
+                                         torch.from_numpy(G).cuda())
+    torch.cuda.synchronize()
+    p = _proj_np(proj)
+    ob = _oracle_bins(p, cam, tiling)
+    og = oracle.blend_backward(cam.width, cam.height, p["mean2d"], p["conic"], p["opacity"], p["rgb"], ob,
+                               G.transpose(1, 2, 0).reshape(-1, 3))
+    for name, got, want in (("mean2d", _np(gm), og.mean2d), ("conic", _np(gco)[:, :3], og.conic),
+                            ("opacity", _np(gco)[:, 3], og.opacity), ("rgb", _np(gc), og.rgb)):
+        rel = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-30)
+        assert rel <= 1e-3, (name, rel)
+
+
+def test_autograd_function():
+    scene, cams = scenes.config_c1()
+    cam = cams[0]
+    _, proj, bins = _gpu_frame(scene, cam, (2, 2))
+    m = proj.mean2d.clone().requires_grad_(True)
+    co = proj.conic_opacity.clone().requires_grad_(True)
+    c = proj.rgb.clone().requires_grad_(True)
+    img = tgs.RasterizeFn.apply(m, co, c, proj.depth, proj.radius, proj.rect, bins, cam.width, cam.height,
+                                (0.0, 0.0, 0.0))
+    loss = img.sum()
+    loss.backward()
+    gm, gco, gc = tgs.rasterize_backward(proj, bins, cam.width, cam.height,
+                                         *tgs.rasterize(proj, bins, cam.width, cam.height, "fp32")[1:],
+                                         torch.ones_like(img))
+    assert torch.allclose(m.grad, gm) and torch.allclose(co.grad, gco) and torch.allclose(c.grad, gc)
+    assert math.isfinite(float(loss))
