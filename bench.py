@@ -209,7 +209,7 @@ def _config(scene, cams, args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tgs", choices=["tgs", "reference"])
     ap.add_argument("--precision", default="fp16_tc", choices=["fp16_tc", "fp32"])

@@ -167,14 +167,15 @@ tgs_status tgs_bin_sort(const tgs_projected* proj, int64_t n, int32_t width, int
   return TGS_OK;
 }
 
-static tgs_status check_raster_args(const tgs_projected* proj, const tgs_bins* bins, int32_t width,
-                                    int32_t height, const tgs_tiling* tiling,
+static tgs_status check_raster_args(const tgs_projected* proj, int64_t n, const tgs_bins* bins,
+                                    int32_t width, int32_t height, const tgs_tiling* tiling,
                                     const tgs_raster_opts* opts) {
-  if (!proj || !bins || !opts || !valid_tiling(tiling) || !valid_size(width, height))
+  if (!proj || !bins || !opts || !valid_tiling(tiling) || !valid_size(width, height) || n < 0 ||
+      n >= (int64_t(1) << 31))
     return set_error("bad argument"), TGS_ERR_INVALID_ARGUMENT;
   if (!bins->ranges || (bins->capacity > 0 && (!bins->vals || !bins->masks)))
     return set_error("null bins array"), TGS_ERR_INVALID_ARGUMENT;
-  if (!proj->mean2d || !proj->conic_opacity || !proj->rgb)
+  if (n > 0 && (!proj->mean2d || !proj->conic_opacity || !proj->rgb))
     return set_error("null projected array"), TGS_ERR_INVALID_ARGUMENT;
   return TGS_OK;
 }
@@ -183,8 +184,7 @@ tgs_status tgs_rasterize(const tgs_projected* proj, int64_t n, const tgs_bins* b
                          int32_t height, const tgs_tiling* tiling, const tgs_raster_opts* opts,
                          float* out_rgb, float* out_T, int32_t* n_contrib, void* stream) {
   g_msg[0] = 0;
-  (void)n;
-  tgs_status s = check_raster_args(proj, bins, width, height, tiling, opts);
+  tgs_status s = check_raster_args(proj, n, bins, width, height, tiling, opts);
   if (s != TGS_OK) return s;
   if (!out_rgb || !out_T) return set_error("null output"), TGS_ERR_INVALID_ARGUMENT;
   s = require_current_sm103();
@@ -210,9 +210,8 @@ tgs_status tgs_rasterize_backward(const tgs_projected* proj, int64_t n, const tg
                                   float* g_mean2d, float* g_conic_opacity, float* g_rgb,
                                   void* stream) {
   g_msg[0] = 0;
-  tgs_status s = check_raster_args(proj, bins, width, height, tiling, opts);
+  tgs_status s = check_raster_args(proj, n, bins, width, height, tiling, opts);
   if (s != TGS_OK) return s;
-  if (n < 0 || n >= (int64_t(1) << 31)) return set_error("bad n"), TGS_ERR_INVALID_ARGUMENT;
   if (!out_T || !n_contrib || !grad_rgb || (n > 0 && (!g_mean2d || !g_conic_opacity || !g_rgb)))
     return set_error("null argument"), TGS_ERR_INVALID_ARGUMENT;
   s = require_current_sm103();

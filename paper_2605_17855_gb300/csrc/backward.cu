@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(1024) k_raster_bwd(
     float* __restrict__ g_mean2d, float* __restrict__ g_co, float* __restrict__ g_rgb) {
   __shared__ float2 s_xy[kBatch];
   __shared__ float4 s_co[kBatch];
+  __shared__ float4 s_L[kBatch];  // Cholesky factor of the conic (same forward arithmetic)
   __shared__ float3 s_rgb[kBatch];
   __shared__ uint16_t s_mask[kBatch];
   __shared__ uint32_t s_idx[kBatch];
@@ -90,7 +91,10 @@ __global__ void __launch_bounds__(1024) k_raster_bwd(
       s_idx[threadIdx.x] = i;
       s_mask[threadIdx.x] = masks[e];
       s_xy[threadIdx.x] = mean2d[i];
-      s_co[threadIdx.x] = conic_opacity[i];
+      const float4 co = conic_opacity[i];
+      const float3 L = conic_factor(co.x, co.y, co.z);
+      s_co[threadIdx.x] = co;
+      s_L[threadIdx.x] = make_float4(L.x, L.y, L.z, 0.f);
       s_rgb[threadIdx.x] = make_float3(rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2]);
     }
     __syncthreads();
@@ -99,6 +103,8 @@ __global__ void __launch_bounds__(1024) k_raster_bwd(
       const uint32_t m = s_mask[j];
       const float2 xy = s_xy[j];
       const float4 co = s_co[j];
+      const float4 Lf = s_L[j];
+      const float3 L = make_float3(Lf.x, Lf.y, Lf.z);
       const float3 c = s_rgb[j];
       float gmx = 0.f, gmy = 0.f, ga = 0.f, gb = 0.f, gc = 0.f, go = 0.f, gr = 0.f, gg = 0.f,
             gbl = 0.f;
@@ -107,7 +113,7 @@ __global__ void __launch_bounds__(1024) k_raster_bwd(
       for (int k = 0; k < PPT; ++k) {
         if (pos > last[k] || !((m >> tile[k]) & 1u)) continue;
         const float dx = __fsub_rn(px[k], xy.x), dy = __fsub_rn(py[k], xy.y);
-        const float power = power_fp32(co.x, co.y, co.z, dx, dy);
+        const float power = power_fp32(L, dx, dy);
         const float ep = ex2(__fmul_rn(power, kLog2e));
         const float oe = __fmul_rn(co.w, ep);
         const float alpha = fminf(kAlphaMax, oe);

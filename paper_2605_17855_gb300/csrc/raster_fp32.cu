@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(1024) k_raster_fp32(
     int gw, int gh, int GX, float3 bg, float* __restrict__ out_rgb, float* __restrict__ out_T,
     int* __restrict__ n_contrib, unsigned long long* __restrict__ counters) {
   __shared__ float2 s_xy[kBatch];
-  __shared__ float4 s_co[kBatch];
+  __shared__ float4 s_co[kBatch];  // Cholesky factor of the conic (l11, l12, l22), opacity
   __shared__ float3 s_rgb[kBatch];
   __shared__ uint16_t s_mask[kBatch];
 
@@ -62,7 +62,9 @@ __global__ void __launch_bounds__(1024) k_raster_fp32(
       const uint32_t i = vals[e];
       s_mask[threadIdx.x] = masks[e];
       s_xy[threadIdx.x] = mean2d[i];
-      s_co[threadIdx.x] = conic_opacity[i];
+      const float4 co = conic_opacity[i];
+      const float3 L = conic_factor(co.x, co.y, co.z);
+      s_co[threadIdx.x] = make_float4(L.x, L.y, L.z, co.w);
       s_rgb[threadIdx.x] = make_float3(rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2]);
     }
     __syncthreads();
@@ -76,7 +78,7 @@ __global__ void __launch_bounds__(1024) k_raster_fp32(
         if (!((m >> tile[k]) & 1u) || st[k].done) continue;
         if (COUNT) ++evaluated;
         const float dx = __fsub_rn((float)px[k], xy.x), dy = __fsub_rn((float)py[k], xy.y);
-        const float power = power_fp32(co.x, co.y, co.z, dx, dy);
+        const float power = power_fp32(make_float3(co.x, co.y, co.z), dx, dy);
         const float alpha = fminf(kAlphaMax, __fmul_rn(co.w, ex2(__fmul_rn(power, kLog2e))));
         if (alpha < kAlphaMin) continue;
         if (COUNT) ++passing;

@@ -2,7 +2,8 @@
 // "Grouped rasterization"; Algorithm 1, the per-group CTA loop), written for sm_103a with tcgen05.
 //
 // One CTA per tile group. The group's depth-sorted list is consumed in chunks of NB entries:
-//   * producer warp: gathers the chunk's Gaussians (mean, conic, opacity, colour, mask) and, for
+//   * producer warps (several, on interleaved chunks): gather the chunk's Gaussians (mean, conic,
+//     opacity, colour, mask) and, for
 //     every member tile whose mask bit is set, writes the Gaussian's coefficient row of the power
 //     expansion about that tile's centre (o_x, o_y) = (16 tx + 8, 16 ty + 8). With pixel offsets
 //     (x, y) = (px - o_x, py - o_y) and (mx, my) = mu' - o:
@@ -26,6 +27,9 @@
 // The chunk is loaded from global memory once per group and reused by all member tiles
 // (the cross-tile reuse of Section 4.4.2); a tile ignores entries whose mask bit is clear, which
 // keeps each tile's front-to-back order (Section 4.4.2, numerical equivalence).
+// Termination: before each chunk the MMA thread checks whether every epilogue warp has finished
+// all its pixels (T < 1e-4 or end of list); if so it stops issuing, raises a stop flag for the
+// producers and signals the epilogue the index of the last job.
 // Every wait on an mbarrier is bounded (2 s); on expiry the CTA records TGS_ERR_TIMEOUT in the
 // device error word, drains its MMAs, frees its tensor memory and exits.
 #include <algorithm>
@@ -41,19 +45,19 @@ constexpr float kLog2AlphaMax = -0.014499569695115089f;  // log2(0.99)
 // Rows whose FP16 hi/lo error bound 2^-22 * sum_k |q_k| max|f_k| exceeds this (in log2 units)
 // are evaluated by the scalar FP32 path.
 constexpr float kMaxWeightedCoef = 4096.0f;
-constexpr int kSlots = 4;
 constexpr int kLBO = 128;  // bytes between the two K core matrices of an 8-row group
 constexpr int kSBO = 256;  // bytes between 8-row groups
 
-template <int GW, int GH, int NWG, int NB>
+template <int GW, int GH, int NWG, int NB, int NPROD>
 struct Cfg {
   static constexpr int kTiles = GW * GH;
   static constexpr int kRounds = kTiles / NWG;
   static_assert(kTiles % NWG == 0, "tiles must split evenly over warpgroups");
   static constexpr int kEpiWarps = 4 * NWG;
-  static constexpr int kThreads = 32 * (kEpiWarps + 2);
-  static constexpr int kProdWarp = kEpiWarps;
-  static constexpr int kMmaWarp = kEpiWarps + 1;
+  static constexpr int kProdWarp0 = kEpiWarps;
+  static constexpr int kMmaWarp = kEpiWarps + NPROD;
+  static constexpr int kThreads = 32 * (kMmaWarp + 1);
+  static constexpr int kSlots = 2 * NPROD;  // each producer owns the slots s with s % NPROD == p
   static constexpr int kStageCols = NWG * 2 * NB;
   static constexpr int kTmemCols = 2 * kStageCols;
   static_assert(kTmemCols == 32 || kTmemCols == 64 || kTmemCols == 128 || kTmemCols == 256 ||
@@ -66,22 +70,23 @@ template <int TILES, int NB>
 struct __align__(16) Slot {
   uint8_t B[TILES][NB * 32];  // K-major canonical, no swizzle: (row/8)*256 + (k/8)*128 + (row%8)*16
   float4 rgbc[NB];            // colour, cap = min(log2 o, log2 0.99)
-  float4 sp0[NB];             // mu'x, mu'y, a, b  (scalar fallback)
-  float2 sp1[NB];             // c, log2 o
+  float4 sp0[NB];             // mu'x, mu'y, l11, l12  (scalar rows; Cholesky factor of the conic)
+  float2 sp1[NB];             // l22, log2 o
   uint32_t tbits[TILES];      // bit j: entry j is used by tile t
   uint32_t sbits[TILES];      // bit j: entry j uses the scalar path for tile t
-  int32_t count;              // valid entries, -1 = end of list
   int32_t base;               // list position of entry 0 relative to the group start
 };
 
-template <int TILES, int NB>
+template <int TILES, int NB, int SLOTS>
 struct __align__(1024) Smem {
   uint8_t A[2][4096];  // two 128-pixel M blocks of the tile feature operand
-  Slot<TILES, NB> slot[kSlots];
-  uint64_t full[kSlots], empty[kSlots], tfull[2], tempty[2], drain;
+  Slot<TILES, NB> slot[SLOTS];
+  uint64_t full[SLOTS], empty[SLOTS], tfull[2], tempty[2], drain;
   uint32_t tmem_base;
-  int abort;
-  int done_warps;
+  int abort;       // a bounded wait expired somewhere in the CTA
+  int stop;        // the MMA thread stopped issuing: producers quit
+  int end_job;     // index of the job whose tfull phase signals the end (-1 until known)
+  int done_warps;  // epilogue warps whose pixels have all finished
 };
 
 // Pixel of TMEM lane m (0..127) of M block h inside a 16x16 tile: warp quarters are 8x4 pixels.
@@ -131,21 +136,22 @@ __device__ __forceinline__ void blend_step(float e, const float4& rc, PixState& 
 __device__ __forceinline__ float scalar_exponent(float px, float py, const float4& p0,
                                                  const float2& p1) {
   const float dx = __fsub_rn(px, p0.x), dy = __fsub_rn(py, p0.y);
-  return fmaf(power_fp32(p0.z, p0.w, p1.x, dx, dy), kLog2e, p1.y);
+  return fmaf(power_fp32(make_float3(p0.z, p0.w, p1.x), dx, dy), kLog2e, p1.y);
 }
 
-template <int GW, int GH, int NWG, int NB, bool COUNT>
-__global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB>::kThreads, 1)
+template <int GW, int GH, int NWG, int NB, int NPROD, bool COUNT>
+__global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB, NPROD>::kThreads, 1)
     k_raster_tc(const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ vals,
                 const uint16_t* __restrict__ masks, const float2* __restrict__ mean2d,
                 const float4* __restrict__ conic_opacity, const float* __restrict__ rgb, int width,
                 int height, int GX, float3 bg, float* __restrict__ out_rgb,
                 float* __restrict__ out_T, int* __restrict__ n_contrib,
                 unsigned long long* __restrict__ counters, int32_t* __restrict__ err) {
-  using C = Cfg<GW, GH, NWG, NB>;
+  using C = Cfg<GW, GH, NWG, NB, NPROD>;
   constexpr int TILES = C::kTiles;
+  constexpr int SLOTS = C::kSlots;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  auto& S = *reinterpret_cast<Smem<TILES, NB>*>(smem_raw);
+  auto& S = *reinterpret_cast<Smem<TILES, NB, SLOTS>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gid = blockIdx.x;
   const int gx = gid % GX, gy = gid / GX;
@@ -166,7 +172,7 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB>::kThreads, 1)
     *reinterpret_cast<uint4*>(rowp + kLBO) = c1;
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kSlots; ++s) {
+    for (int s = 0; s < SLOTS; ++s) {
       mbar_init(&S.full[s], 1);
       mbar_init(&S.empty[s], C::kEpiWarps + 1);
     }
@@ -176,6 +182,8 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB>::kThreads, 1)
     }
     mbar_init(&S.drain, 1);
     S.abort = 0;
+    S.stop = 0;
+    S.end_job = -1;
     S.done_warps = 0;
     fence_mbarrier_init();
   }
@@ -189,21 +197,23 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB>::kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = S.tmem_base;
   volatile int* abort_flag = &S.abort;
+  volatile int* stop_flag = &S.stop;
 
   const uint32_t list_start = ranges[2 * gid], list_end = ranges[2 * gid + 1];
   const int nchunks = (int)((list_end - list_start + NB - 1) / NB);
 
-  if (warp == C::kProdWarp) {
-    // ---- producer: gather + coefficient rows ------------------------------------------------
-    int c = 0;
-    for (; c < nchunks; ++c) {
-      // warp-uniform decision: every epilogue warp has finished all its pixels
-      const int dw = __shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(&S.done_warps), 0);
-      if (dw >= C::kEpiWarps) break;
-      const int s = c % kSlots;
-      const uint32_t par = ((c / kSlots) & 1) ^ 1;
-      bool ok = mbar_wait_bounded(&S.empty[s], par, abort_flag, kWaitLimitNs);
-      if (!__all_sync(0xffffffffu, ok)) { record_abort(&S.abort, err); break; }
+  if (warp >= C::kProdWarp0 && warp < C::kMmaWarp) {
+    // ---- producers: gather + coefficient rows, chunks c = p, p + NPROD, ... ------------------
+    for (int c = warp - C::kProdWarp0; c < nchunks; c += NPROD) {
+      const int s = c % SLOTS;
+      const int w = mbar_wait_or_stop(&S.empty[s], ((c / SLOTS) & 1) ^ 1, stop_flag, abort_flag,
+                                      kWaitLimitNs);
+      const int wmax = __reduce_max_sync(0xffffffffu, w);
+      if (wmax == 1 && __reduce_min_sync(0xffffffffu, w) >= 1) break;  // stopped: not an error
+      if (wmax != 0) {
+        if (wmax == 2) record_abort(&S.abort, err);
+        break;
+      }
       auto& sl = S.slot[s];
       const uint32_t e = list_start + (uint32_t)c * NB + lane;
       const bool valid = e < list_end;
@@ -219,9 +229,10 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB>::kThreads, 1)
         col = make_float3(rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2]);
       }
       const float lo2 = lg2(co.w);
+      const float3 Lc = valid ? conic_factor(co.x, co.y, co.z) : make_float3(0.f, 0.f, 0.f);
       sl.rgbc[lane] = make_float4(col.x, col.y, col.z, fminf(lo2, kLog2AlphaMax));
-      sl.sp0[lane] = make_float4(mu.x, mu.y, co.x, co.y);
-      sl.sp1[lane] = make_float2(co.z, lo2);
+      sl.sp0[lane] = make_float4(mu.x, mu.y, Lc.x, Lc.y);
+      sl.sp1[lane] = make_float2(Lc.z, lo2);
 #pragma unroll
       for (int t = 0; t < TILES; ++t) {
         const int tx = gx * GW + (t % GW), ty = gy * GH + (t / GW);
@@ -230,14 +241,17 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB>::kThreads, 1)
         uint4 r0 = make_uint4(0u, 0u, 0u, 0u), r1 = make_uint4(0u, 0u, 0u, 0u);
         if (active) {
           const float mx = mu.x - (float)(tx * kTile + 8), my = mu.y - (float)(ty * kTile + 8);
-          const float a = co.x, b = co.y, cc = co.z;
+          // (u, v) = L m: the linear and constant terms are formed from it (conic m = L^T L m and
+          // m^T conic m = u^2 + v^2), which avoids the cancellation of the expanded products when
+          // the tile is far from the centre of a thin splat
+          const float u = fmaf(Lc.x, mx, Lc.y * my), v = Lc.z * my;
           float q[6];
-          q[0] = -0.5f * a * kLog2e;
-          q[1] = -b * kLog2e;
-          q[2] = -0.5f * cc * kLog2e;
-          q[3] = (a * mx + b * my) * kLog2e;
-          q[4] = (b * mx + cc * my) * kLog2e;
-          q[5] = -0.5f * (a * mx * mx + 2.f * b * mx * my + cc * my * my) * kLog2e + lo2;
+          q[0] = -0.5f * co.x * kLog2e;
+          q[1] = -co.y * kLog2e;
+          q[2] = -0.5f * co.z * kLog2e;
+          q[3] = Lc.x * u * kLog2e;
+          q[4] = fmaf(Lc.y, u, Lc.z * v) * kLog2e;
+          q[5] = fmaf(-0.5f * kLog2e, fmaf(u, u, v * v), lo2);
           const float wsum = 64.f * (fabsf(q[0]) + fabsf(q[1]) + fabsf(q[2])) +
                              8.f * (fabsf(q[3]) + fabsf(q[4])) + fabsf(q[5]);
           scalar = !(wsum <= kMaxWeightedCoef);
@@ -263,27 +277,10 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB>::kThreads, 1)
           sl.sbits[t] = sb;
         }
       }
-      if (lane == 0) {
-        sl.count = (int)min((uint32_t)NB, list_end - (list_start + (uint32_t)c * NB));
-        sl.base = c * NB;
-      }
+      if (lane == 0) sl.base = c * NB;
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.full[s]);
-    }
-    // end-of-list marker
-    if (!__shfl_sync(0xffffffffu, *abort_flag, 0)) {
-      const int s = c % kSlots;
-      const uint32_t par = ((c / kSlots) & 1) ^ 1;
-      bool ok = mbar_wait_bounded(&S.empty[s], par, abort_flag, kWaitLimitNs);
-      if (!__all_sync(0xffffffffu, ok)) {
-        record_abort(&S.abort, err);
-      } else {
-        if (lane == 0) {
-          S.slot[s].count = -1;
-          mbar_arrive(&S.full[s]);
-        }
-      }
     }
   } else if (warp == C::kMmaWarp) {
     // ---- MMA issuer ---------------------------------------------------------------------------
@@ -292,19 +289,19 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB>::kThreads, 1)
       const uint64_t adesc0 = smem_desc(smem_addr(&S.A[0][0]), kLBO, kSBO);
       const uint64_t adesc1 = smem_desc(smem_addr(&S.A[1][0]), kLBO, kSBO);
       int job = 0;
-      for (int c = 0;; ++c) {
-        const int s = c % kSlots;
-        if (!mbar_wait_bounded(&S.full[s], (c / kSlots) & 1, abort_flag, kWaitLimitNs)) {
-          record_abort(&S.abort, err);
+      bool failed = false;
+      for (int c = 0; c < nchunks && !failed; ++c) {
+        // every epilogue warp has finished all its pixels: no more work for this group
+        if (*reinterpret_cast<volatile int*>(&S.done_warps) >= C::kEpiWarps) break;
+        const int s = c % SLOTS;
+        if (!mbar_wait_bounded(&S.full[s], (c / SLOTS) & 1, abort_flag, kWaitLimitNs)) {
+          failed = true;
           break;
         }
         auto& sl = S.slot[s];
-        if (sl.count < 0) break;
-        bool failed = false;
         for (int r = 0; r < C::kRounds; ++r, ++job) {
           const int st = job & 1;
           if (!mbar_wait_bounded(&S.tempty[st], ((job >> 1) & 1) ^ 1, abort_flag, kWaitLimitNs)) {
-            record_abort(&S.abort, err);
             failed = true;
             break;
           }
@@ -320,8 +317,20 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB>::kThreads, 1)
           }
           mma_commit(&S.tfull[st]);
         }
-        if (failed) break;
-        mma_commit(&S.empty[s]);
+        if (!failed) mma_commit(&S.empty[s]);
+      }
+      *stop_flag = 1;
+      if (failed) {
+        record_abort(&S.abort, err);
+      } else {
+        // end signal: complete the next tfull phase with a plain arrive after publishing its index
+        const int st = job & 1;
+        if (mbar_wait_bounded(&S.tempty[st], ((job >> 1) & 1) ^ 1, abort_flag, kWaitLimitNs)) {
+          *reinterpret_cast<volatile int*>(&S.end_job) = job;
+          mbar_arrive(&S.tfull[st]);
+        } else {
+          record_abort(&S.abort, err);
+        }
       }
       // drain: all MMAs issued by this thread have completed before tensor memory is freed
       mma_commit(&S.drain);
@@ -354,21 +363,27 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB>::kThreads, 1)
     bool counted_done = false;
     unsigned long long evaluated = 0, passing = 0;
     int job = 0;
-    for (int c = 0;; ++c) {
-      const int s = c % kSlots;
-      bool ok = mbar_wait_bounded(&S.full[s], (c / kSlots) & 1, abort_flag, kWaitLimitNs);
-      if (!__all_sync(0xffffffffu, ok)) { record_abort(&S.abort, err); break; }
-      auto& sl = S.slot[s];
-      const int cnt = sl.count;
-      if (cnt < 0) break;
-      bool failed = false;
+    bool finished = false;
+    for (int c = 0; !finished; ++c) {
+      const int s = c % SLOTS;
 #pragma unroll
       for (int r = 0; r < C::kRounds; ++r) {
         const int st = job & 1;
-        ok = mbar_wait_bounded(&S.tfull[st], (job >> 1) & 1, abort_flag, kWaitLimitNs);
+        bool ok = mbar_wait_bounded(&S.tfull[st], (job >> 1) & 1, abort_flag, kWaitLimitNs);
+        if (!__all_sync(0xffffffffu, ok)) { record_abort(&S.abort, err); finished = true; break; }
+        if (__shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(&S.end_job), 0) == job) {
+          finished = true;
+          break;
+        }
+        if (r == 0) {
+          // the slot's producer writes (colours, masks) are complete: the MMA thread waited on
+          // the same phase before issuing this job
+          ok = mbar_wait_bounded(&S.full[s], (c / SLOTS) & 1, abort_flag, kWaitLimitNs);
+          if (!__all_sync(0xffffffffu, ok)) { record_abort(&S.abort, err); finished = true; break; }
+        }
         ++job;
-        if (!__all_sync(0xffffffffu, ok)) { record_abort(&S.abort, err); failed = true; break; }
         tc_fence_after();
+        auto& sl = S.slot[s];
         const int t = wg + NWG * r;
         const uint32_t tb = sl.tbits[t];
         const bool work = tb != 0u && !wdone[r];
@@ -411,11 +426,12 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB>::kThreads, 1)
           __syncwarp();
           if (lane == 0) mbar_arrive(&S.tempty[st]);
         }
+        if (r == C::kRounds - 1) {
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&S.empty[s]);
+        }
       }
-      if (failed) break;
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&S.empty[s]);
-      if (!counted_done) {
+      if (!finished && !counted_done) {
         bool all = true;
 #pragma unroll
         for (int r = 0; r < C::kRounds; ++r) all &= wdone[r];
@@ -459,12 +475,12 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB>::kThreads, 1)
   if (warp == C::kMmaWarp) tmem_dealloc(tmem, C::kTmemCols);
 }
 
-template <int GW, int GH, int NWG, int NB>
+template <int GW, int GH, int NWG, int NB, int NPROD>
 tgs_status launch_cfg(const tgs_projected& p, const tgs_bins& b, int width, int height,
                       const tgs_raster_opts& o, float* out_rgb, float* out_T, int32_t* n_contrib,
                       cudaStream_t st) {
-  using Cf = Cfg<GW, GH, NWG, NB>;
-  using Sm = Smem<GW * GH, NB>;
+  using Cf = Cfg<GW, GH, NWG, NB, NPROD>;
+  using Sm = Smem<GW * GH, NB, Cf::kSlots>;
   const int TX = div_up(width, kTile), TY = div_up(height, kTile);
   const int GX = div_up(TX, GW), GY = div_up(TY, GH);
   // Limit residency so that co-resident CTAs never wait on each other's tensor memory:
@@ -483,12 +499,12 @@ tgs_status launch_cfg(const tgs_projected& p, const tgs_bins& b, int width, int 
   const float3 bg = make_float3(o.bg[0], o.bg[1], o.bg[2]);
   int32_t* err = device_error_word();
   if (count) {
-    auto* k = k_raster_tc<GW, GH, NWG, NB, true>;
+    auto* k = k_raster_tc<GW, GH, NWG, NB, NPROD, true>;
     TGS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<GX * GY, Cf::kThreads, smem, st>>>(b.ranges, b.vals, b.masks, m2, co, p.rgb, width, height, GX,
                                            bg, out_rgb, out_T, n_contrib, cnt, err);
   } else {
-    auto* k = k_raster_tc<GW, GH, NWG, NB, false>;
+    auto* k = k_raster_tc<GW, GH, NWG, NB, NPROD, false>;
     TGS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<GX * GY, Cf::kThreads, smem, st>>>(b.ranges, b.vals, b.masks, m2, co, p.rgb, width, height, GX,
                                            bg, out_rgb, out_T, n_contrib, cnt, err);
@@ -504,11 +520,11 @@ tgs_status launch_raster_tc(const tgs_projected& p, const tgs_bins& b, int width
                             int32_t* n_contrib, cudaStream_t st) {
   if (((uintptr_t)p.mean2d & 7) || ((uintptr_t)p.conic_opacity & 15))
     return set_error("mean2d needs 8-byte and conic_opacity 16-byte alignment"), TGS_ERR_INVALID_ARGUMENT;
-  if (gw == 1 && gh == 1) return launch_cfg<1, 1, 1, 32>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
-  if (gw == 2 && gh == 2) return launch_cfg<2, 2, 4, 32>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
-  if (gw == 4 && gh == 2) return launch_cfg<4, 2, 4, 32>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
-  if (gw == 2 && gh == 4) return launch_cfg<2, 4, 4, 32>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
-  if (gw == 4 && gh == 4) return launch_cfg<4, 4, 4, 32>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
+  if (gw == 1 && gh == 1) return launch_cfg<1, 1, 1, 32, 2>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
+  if (gw == 2 && gh == 2) return launch_cfg<2, 2, 4, 32, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
+  if (gw == 4 && gh == 2) return launch_cfg<4, 2, 4, 32, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
+  if (gw == 2 && gh == 4) return launch_cfg<2, 4, 4, 32, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
+  if (gw == 4 && gh == 4) return launch_cfg<4, 4, 4, 32, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
   set_error("tensor-core path supports groups 1x1, 2x2, 4x2, 2x4, 4x4 (got %dx%d)", gw, gh);
   return TGS_ERR_INVALID_ARGUMENT;
 }

@@ -76,14 +76,26 @@ __device__ __forceinline__ float lg2(float x) {
   return y;
 }
 
-// Power of Eq. tensorgs_power_scalar, -1/2 (a dx^2 + c dy^2) - b dx dy, with a fixed operation
-// order (no contraction choices left to the compiler), clamped at 0 (a positive value can only come
-// from rounding). The FP32 forward, the backward replay and the scalar fallback of the tensor path
-// all call this, so their decisions agree bit for bit.
-__device__ __forceinline__ float power_fp32(float a, float b, float c, float dx, float dy) {
-  const float s = __fmaf_rn(__fmul_rn(a, dx), dx, __fmul_rn(__fmul_rn(c, dy), dy));
-  const float p = __fmaf_rn(-0.5f, s, -__fmul_rn(__fmul_rn(b, dx), dy));
-  return fminf(p, 0.f);
+// Upper Cholesky factor L = [[l11, l12], [0, l22]] of a conic [[a, b], [b, c]] (conic = L^T L),
+// computed once per list entry. The determinant a c - b^2 uses Kahan's compensated 2x2 scheme
+// (one FMA recovers the rounding error of b^2), so thin splats, whose determinant is a small
+// difference of large products, keep full relative accuracy.
+__device__ __forceinline__ float3 conic_factor(float a, float b, float c) {
+  const float w = __fmul_rn(b, b);
+  const float e = __fmaf_rn(-b, b, w);  // w - b*b, exactly
+  const float det = __fadd_rn(__fmaf_rn(a, c, -w), e);
+  const float l11 = sqrtf(a);
+  return make_float3(l11, __fdiv_rn(b, l11), sqrtf(fmaxf(__fdiv_rn(det, a), 0.f)));
+}
+
+// Power of Eq. power, -1/2 d^T conic d, evaluated as -1/2 |L d|^2: a sum of two squares, so it is
+// never positive and does not suffer the cancellation of the expanded form of
+// Eq. tensorgs_power_scalar when d is large along a thin splat. Fixed operation order: the FP32
+// forward, the backward replay and the scalar rows of the tensor path agree bit for bit.
+__device__ __forceinline__ float power_fp32(float3 L, float dx, float dy) {
+  const float u = __fmaf_rn(L.x, dx, __fmul_rn(L.y, dy));
+  const float v = __fmul_rn(L.z, dy);
+  return __fmul_rn(-0.5f, __fmaf_rn(u, u, __fmul_rn(v, v)));
 }
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
@@ -124,6 +136,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
     if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+// Bounded wait that also ends when *stop is set: 0 = phase complete, 1 = stopped, 2 = timed out
+// or aborted.
+__device__ __forceinline__ int mbar_wait_or_stop(uint64_t* bar, uint32_t parity, volatile int* stop,
+                                                 volatile int* abort, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return 0;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return 0;
+    if (*stop) return 1;
+    if (*abort) return 2;
+    if (globaltimer_ns() - t0 > limit_ns) return 2;
   }
 }
 
