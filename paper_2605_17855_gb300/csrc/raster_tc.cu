@@ -1,12 +1,13 @@
 // Grouped tensor-core rasterizer (Section 4.2 "Tensorizing the power computation" and Section 4.4.2
 // "Grouped rasterization"; Algorithm 1, the per-group CTA loop), written for sm_103a with tcgen05.
 //
-// One CTA per tile group. The group's depth-sorted list is consumed in chunks of NB entries:
+// One CTA per tile group. The group's depth-sorted list is consumed in chunks of NB = 32 entries:
 //   * producer warps (several, on interleaved chunks): gather the chunk's Gaussians (mean, conic,
-//     opacity, colour, mask) and, for
-//     every member tile whose mask bit is set, writes the Gaussian's coefficient row of the power
-//     expansion about that tile's centre (o_x, o_y) = (16 tx + 8, 16 ty + 8). With pixel offsets
-//     (x, y) = (px - o_x, py - o_y) and (mx, my) = mu' - o:
+//     opacity, colour, mask). For every member tile, the entries whose mask bit is set are packed
+//     to the front (Section 4.4.2: "select Gaussian entries whose bit mask includes t"), and for
+//     each the producer writes the Gaussian's coefficient row of the power expansion about the
+//     tile's centre (o_x, o_y) = (16 tx + 8, 16 ty + 8). With pixel offsets (x, y) = (px - o_x,
+//     py - o_y) and (mx, my) = mu' - o:
 //        log2(o) + log2(e) * power = q . [x^2, xy, y^2, x, y, 1]
 //        q = log2(e) * (-a/2, -b, -c/2, a mx + b my, b mx + c my, -(a mx^2 + 2 b mx my + c my^2)/2)
 //            + (0, 0, 0, 0, 0, log2 o)
@@ -16,17 +17,18 @@
 //     [hi(6), lo(6), 0, 0, 0, 0] against features [f(6), f(6), 0, 0, 0, 0]: the zero padding of
 //     Section 4.2.3 (exact), with the padding slots used for the lo half. |x|, |y| <= 8, so every
 //     feature is an exact FP16 integer. Rows whose FP16 error bound is too large take a scalar
-//     FP32 path in the epilogue instead.
-//   * MMA thread: per tile, D[128 px x NB] = A_h[128 x 16] * B_t[NB x 16]^T with
-//     tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = NB, K = 16), FP32 accumulators in tensor
+//     FP32 path in the epilogue instead. The producers are software-pipelined two chunks deep.
+//   * MMA thread: per tile, D[128 px x 32] = A_h[128 x 16] * B_t[32 x 16]^T with
+//     tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 32, K = 16), FP32 accumulators in tensor
 //     memory, double-buffered; completion signalled through tcgen05.commit on mbarriers.
 //   * epilogue warpgroups (one per tile of a round): each thread owns one TMEM lane = one pixel in
-//     each of the tile's two 128-pixel M blocks, loads its NB exponents with tcgen05.ld and runs
-//     the front-to-back blend of Section 2 in FP32 (skip if alpha < 1/255 tested in the log2
-//     domain before the exp, alpha = min(0.99, 2^D), stop when T' < 1e-4 without blending).
+//     each of the tile's two 128-pixel M blocks, streams the tile's exponents out of tensor memory
+//     8 columns at a time (the next load in flight while the current columns are blended) and runs
+//     the front-to-back blend of Section 2 in FP32: skip if alpha < 1/255 (tested in the log2
+//     domain before the exp), alpha = min(0.99, 2^D), stop when T' < 1e-4 without blending.
 // The chunk is loaded from global memory once per group and reused by all member tiles
-// (the cross-tile reuse of Section 4.4.2); a tile ignores entries whose mask bit is clear, which
-// keeps each tile's front-to-back order (Section 4.4.2, numerical equivalence).
+// (the cross-tile reuse of Section 4.4.2); packing a tile's entries keeps their order, hence each
+// tile's front-to-back order (Section 4.4.2, numerical equivalence with per-tile rasterization).
 // Termination: before each chunk the MMA thread checks whether every epilogue warp has finished
 // all its pixels (T < 1e-4 or end of list); if so it stops issuing, raises a stop flag for the
 // producers and signals the epilogue the index of the last job.
@@ -40,15 +42,18 @@ namespace tgs {
 namespace {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
-constexpr float kL255 = -7.994353436858858f;  // log2(1/255)
+constexpr float kL255 = -7.994353436858858f;            // log2(1/255)
 constexpr float kLog2AlphaMax = -0.014499569695115089f;  // log2(0.99)
 // Rows whose FP16 hi/lo error bound 2^-22 * sum_k |q_k| max|f_k| exceeds this (in log2 units)
 // are evaluated by the scalar FP32 path.
 constexpr float kMaxWeightedCoef = 4096.0f;
 constexpr int kLBO = 128;  // bytes between the two K core matrices of an 8-row group
 constexpr int kSBO = 256;  // bytes between 8-row groups
+constexpr int NB = 32;     // list entries per chunk = MMA N
 
-template <int GW, int GH, int NWG, int NB, int NPROD>
+__device__ __forceinline__ float inf_f() { return __int_as_float(0x7f800000); }
+
+template <int GW, int GH, int NWG, int NPROD>
 struct Cfg {
   static constexpr int kTiles = GW * GH;
   static constexpr int kRounds = kTiles / NWG;
@@ -57,30 +62,31 @@ struct Cfg {
   static constexpr int kProdWarp0 = kEpiWarps;
   static constexpr int kMmaWarp = kEpiWarps + NPROD;
   static constexpr int kThreads = 32 * (kMmaWarp + 1);
-  static constexpr int kSlots = 2 * NPROD;  // each producer owns the slots s with s % NPROD == p
+  static constexpr int kSlots = 2 * NPROD;  // chunk c uses slot c % kSlots, produced by c % NPROD
   static constexpr int kStageCols = NWG * 2 * NB;
   static constexpr int kTmemCols = 2 * kStageCols;
   static_assert(kTmemCols == 32 || kTmemCols == 64 || kTmemCols == 128 || kTmemCols == 256 ||
                     kTmemCols == 512,
                 "TMEM allocation must be a power of two in [32, 512]");
-  static_assert(NB == 32, "the producer maps one list entry to one lane of its warp");
 };
 
-template <int TILES, int NB>
+template <int TILES>
 struct __align__(16) Slot {
-  uint8_t B[TILES][NB * 32];  // K-major canonical, no swizzle: (row/8)*256 + (k/8)*128 + (row%8)*16
-  float4 rgbc[NB];            // colour, cap = min(log2 o, log2 0.99)
-  float4 sp0[NB];             // mu'x, mu'y, l11, l12  (scalar rows; Cholesky factor of the conic)
+  uint8_t B[TILES][NB * 32];  // per tile, packed rows; K-major canonical, no swizzle:
+                              // (row/8)*256 + (k/8)*128 + (row%8)*16
+  float4 rgbc[TILES][NB];     // packed entry k of tile t: colour, min(log2 o, log2 0.99)
+  float4 sp0[NB];             // chunk entry: mu'x, mu'y, l11, l12 (scalar rows; conic factor)
   float2 sp1[NB];             // l22, log2 o
-  uint32_t tbits[TILES];      // bit j: entry j is used by tile t
-  uint32_t sbits[TILES];      // bit j: entry j uses the scalar path for tile t
-  int32_t base;               // list position of entry 0 relative to the group start
+  uint8_t entry[TILES][NB];   // chunk entry (0..31) of packed entry k of tile t
+  uint32_t cnt[TILES];        // packed entries of tile t
+  uint32_t sbits[TILES];      // bit k: packed entry k of tile t uses the scalar path
+  int32_t base;               // list position of chunk entry 0 relative to the group start
 };
 
-template <int TILES, int NB, int SLOTS>
+template <int TILES, int SLOTS>
 struct __align__(1024) Smem {
   uint8_t A[2][4096];  // two 128-pixel M blocks of the tile feature operand
-  Slot<TILES, NB> slot[SLOTS];
+  Slot<TILES> slot[SLOTS];
   uint64_t full[SLOTS], empty[SLOTS], tfull[2], tempty[2], drain;
   uint32_t tmem_base;
   int abort;       // a bounded wait expired somewhere in the CTA
@@ -106,52 +112,108 @@ __device__ __forceinline__ void record_abort(int* abort_flag, int32_t* err) {
   if (err) atomicExch(err, TGS_ERR_TIMEOUT);
 }
 
+// Blend state of one pixel. `thr` is log2(1/255) while the pixel is live and +inf once it has
+// terminated, so the pruning test alone also skips finished pixels.
 struct PixState {
-  float T, r, g, b;
+  float T, r, g, b, thr;
   int last;
-  bool done;
 };
 
+// Scalar FP32 exponents of a packed entry whose FP16 coefficients would be too inaccurate.
+__device__ __noinline__ float2 scalar_exponents(float px0, float py0, float px1, float py1,
+                                                float4 p0, float2 p1) {
+  const float3 L = make_float3(p0.z, p0.w, p1.x);
+  const float e0 = fmaf(power_fp32(L, __fsub_rn(px0, p0.x), __fsub_rn(py0, p0.y)), kLog2e, p1.y);
+  const float e1 = fmaf(power_fp32(L, __fsub_rn(px1, p0.x), __fsub_rn(py1, p0.y)), kLog2e, p1.y);
+  return make_float2(e0, e1);
+}
+
+// One front-to-back step (Section 2) for one pixel, predicated. The caller has voted that some lane
+// of the warp may pass; the pruning test is repeated here against the pixel's live threshold.
+// D = log2(o e^power) already contains the opacity, so alpha = min(0.99, 2^D) = 2^min(D, log2 0.99).
 template <bool COUNT>
 __device__ __forceinline__ void blend_step(float e, const float4& rc, PixState& s, int pos,
                                            unsigned long long& passing) {
-  const float d = fminf(e, rc.w);
-  if (!s.done && d >= kL255) {
-    if (COUNT) ++passing;
-    const float a = ex2(d);
-    const float Tn = fmaf(-s.T, a, s.T);
-    if (Tn < kTMin) {
-      s.done = true;
-    } else {
-      const float w = a * s.T;
-      s.r = fmaf(w, rc.x, s.r);
-      s.g = fmaf(w, rc.y, s.g);
-      s.b = fmaf(w, rc.z, s.b);
-      s.T = Tn;
-      s.last = pos;
+  const bool p = e >= s.thr;                 // alpha >= 1/255 and the pixel is live
+  if (COUNT) passing += p;
+  const float a = ex2(fminf(e, kLog2AlphaMax));
+  const float Tn = fmaf(-s.T, a, s.T);       // T (1 - alpha)
+  const bool term = p && (Tn < kTMin);       // early termination: this entry is not blended
+  if (p && !term) {
+    const float w = a * s.T;
+    s.r = fmaf(w, rc.x, s.r);
+    s.g = fmaf(w, rc.y, s.g);
+    s.b = fmaf(w, rc.z, s.b);
+    s.T = Tn;
+    s.last = pos;
+  }
+  if (term) s.thr = inf_f();
+}
+
+// Blends one 8-column granule (packed entries 8g .. 8g+7 of tile t) into the thread's two pixels.
+// d[0..7] are pixel 0's exponents, d[8..15] pixel 1's. All sixteen prune tests and warp votes are
+// issued before any blend so that they pipeline; padded columns (>= cnt) hold a never-passing
+// exponent.
+template <int TILES, bool COUNT>
+__device__ __forceinline__ void blend_granule(const uint32_t (&d)[16], int g, int cnt, uint32_t sb,
+                                              int base, const Slot<TILES>& sl, int t, int tx,
+                                              int ty, int quarter, int lane, PixState& s0,
+                                              PixState& s1, unsigned long long& evaluated,
+                                              unsigned long long& passing) {
+  float e0[8], e1[8];
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    e0[jj] = __uint_as_float(d[jj]);
+    e1[jj] = __uint_as_float(d[8 + jj]);
+  }
+  const uint32_t sbg = (sb >> (8 * g)) & 0xffu;
+  if (sbg) {  // rare: rows whose FP16 coefficients would be too inaccurate
+    int lx0, ly0, lx1, ly1;
+    lane_pixel(0, quarter * 32 + lane, lx0, ly0);
+    lane_pixel(1, quarter * 32 + lane, lx1, ly1);
+    const float px0 = (float)(tx * kTile + lx0), py0 = (float)(ty * kTile + ly0);
+    const float px1 = (float)(tx * kTile + lx1), py1 = (float)(ty * kTile + ly1);
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj)
+      if ((sbg >> jj) & 1u) {
+        const int en = sl.entry[t][8 * g + jj];
+        const float2 es = scalar_exponents(px0, py0, px1, py1, sl.sp0[en], sl.sp1[en]);
+        e0[jj] = es.x;
+        e1[jj] = es.y;
+      }
+  }
+  bool v0[8], v1[8];
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    v0[jj] = __any_sync(0xffffffffu, e0[jj] >= s0.thr);
+    v1[jj] = __any_sync(0xffffffffu, e1[jj] >= s1.thr);
+  }
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    if (COUNT && 8 * g + jj < cnt) evaluated += (s0.thr < inf_f()) + (s1.thr < inf_f());
+    if (v0[jj] || v1[jj]) {
+      const int j = 8 * g + jj;
+      const float4 rc = sl.rgbc[t][j];
+      const int pos = base + (int)sl.entry[t][j] + 1;
+      if (v0[jj]) blend_step<COUNT>(e0[jj], rc, s0, pos, passing);
+      if (v1[jj]) blend_step<COUNT>(e1[jj], rc, s1, pos, passing);
     }
   }
 }
 
-__device__ __forceinline__ float scalar_exponent(float px, float py, const float4& p0,
-                                                 const float2& p1) {
-  const float dx = __fsub_rn(px, p0.x), dy = __fsub_rn(py, p0.y);
-  return fmaf(power_fp32(make_float3(p0.z, p0.w, p1.x), dx, dy), kLog2e, p1.y);
-}
-
-template <int GW, int GH, int NWG, int NB, int NPROD, bool COUNT>
-__global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB, NPROD>::kThreads, 1)
+template <int GW, int GH, int NWG, int NPROD, bool COUNT>
+__global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD>::kThreads, 1)
     k_raster_tc(const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ vals,
                 const uint16_t* __restrict__ masks, const float2* __restrict__ mean2d,
                 const float4* __restrict__ conic_opacity, const float* __restrict__ rgb, int width,
                 int height, int GX, float3 bg, float* __restrict__ out_rgb,
                 float* __restrict__ out_T, int* __restrict__ n_contrib,
                 unsigned long long* __restrict__ counters, int32_t* __restrict__ err) {
-  using C = Cfg<GW, GH, NWG, NB, NPROD>;
+  using C = Cfg<GW, GH, NWG, NPROD>;
   constexpr int TILES = C::kTiles;
   constexpr int SLOTS = C::kSlots;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  auto& S = *reinterpret_cast<Smem<TILES, NB, SLOTS>*>(smem_raw);
+  auto& S = *reinterpret_cast<Smem<TILES, SLOTS>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gid = blockIdx.x;
   const int gx = gid % GX, gy = gid / GX;
@@ -203,42 +265,79 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB, NPROD>::kThreads, 1)
   const int nchunks = (int)((list_end - list_start + NB - 1) / NB);
 
   if (warp >= C::kProdWarp0 && warp < C::kMmaWarp) {
-    // ---- producers: gather + coefficient rows, chunks c = p, p + NPROD, ... ------------------
-    for (int c = warp - C::kProdWarp0; c < nchunks; c += NPROD) {
+    // ---- producers: gather, pack per tile, coefficient rows; chunks c = p, p + NPROD, ... -------
+    // Software pipeline, two chunks deep: while chunk c is packed, the Gaussian gathers of chunk
+    // c + NPROD and the index/mask loads of chunk c + 2 NPROD are in flight.
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    auto load_index = [&](int c, uint32_t& idx, uint32_t& msk, bool& valid) {
+      const uint32_t e = list_start + (uint32_t)c * NB + lane;
+      valid = c < nchunks && e < list_end;
+      idx = valid ? vals[e] : 0u;
+      msk = valid ? (uint32_t)masks[e] : 0u;
+    };
+    struct Gathered {
+      float2 mu;
+      float4 co;
+      float3 col;
+    };
+    auto gather = [&](uint32_t idx, bool valid, Gathered& g) {
+      g.mu = valid ? mean2d[idx] : make_float2(0.f, 0.f);
+      g.co = valid ? conic_opacity[idx] : make_float4(0.f, 0.f, 0.f, 1.f);
+      g.col = valid ? make_float3(rgb[3 * idx], rgb[3 * idx + 1], rgb[3 * idx + 2])
+                    : make_float3(0.f, 0.f, 0.f);
+    };
+    int c = warp - C::kProdWarp0;
+    uint32_t idx_a, msk_a, idx_b, msk_b;
+    bool val_a, val_b;
+    load_index(c, idx_a, msk_a, val_a);
+    Gathered g_a;
+    gather(idx_a, val_a, g_a);
+    load_index(c + NPROD, idx_b, msk_b, val_b);
+    for (; c < nchunks; c += NPROD) {
+      Gathered g_b;
+      gather(idx_b, val_b, g_b);  // chunk c + NPROD
+      uint32_t idx_c, msk_c;
+      bool val_c;
+      load_index(c + 2 * NPROD, idx_c, msk_c, val_c);
       const int s = c % SLOTS;
       const int w = mbar_wait_or_stop(&S.empty[s], ((c / SLOTS) & 1) ^ 1, stop_flag, abort_flag,
                                       kWaitLimitNs);
-      const int wmax = __reduce_max_sync(0xffffffffu, w);
-      if (wmax == 1 && __reduce_min_sync(0xffffffffu, w) >= 1) break;  // stopped: not an error
-      if (wmax != 0) {
-        if (wmax == 2) record_abort(&S.abort, err);
+      const unsigned wmax = __reduce_max_sync(0xffffffffu, (unsigned)w);
+      if (wmax != 0u) {  // stopped (not an error) or timed out
+        if (wmax == 2u) record_abort(&S.abort, err);
         break;
       }
       auto& sl = S.slot[s];
-      const uint32_t e = list_start + (uint32_t)c * NB + lane;
-      const bool valid = e < list_end;
-      float2 mu = make_float2(0.f, 0.f);
-      float4 co = make_float4(0.f, 0.f, 0.f, 1.f);
-      float3 col = make_float3(0.f, 0.f, 0.f);
-      uint32_t msk = 0;
-      if (valid) {
-        const uint32_t i = vals[e];
-        msk = masks[e];
-        mu = mean2d[i];
-        co = conic_opacity[i];
-        col = make_float3(rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2]);
-      }
+      const bool valid = val_a;
+      const uint32_t msk = msk_a;
+      const float2 mu = g_a.mu;
+      const float4 co = g_a.co;
       const float lo2 = lg2(co.w);
-      const float3 Lc = valid ? conic_factor(co.x, co.y, co.z) : make_float3(0.f, 0.f, 0.f);
-      sl.rgbc[lane] = make_float4(col.x, col.y, col.z, fminf(lo2, kLog2AlphaMax));
+      // Cholesky factor of the conic (used for the linear/constant terms and the scalar rows);
+      // here from the hardware reciprocal square root, the determinant by Kahan's scheme
+      float3 Lc = make_float3(0.f, 0.f, 0.f);
+      if (valid) {
+        const float inv = rsqrtf(co.x);
+        const float w2 = co.y * co.y;
+        const float det = fmaf(co.x, co.z, -w2) + fmaf(-co.y, co.y, w2);
+        const float dp = fmaxf(det, 0.f);
+        Lc = make_float3(co.x * inv, co.y * inv, dp > 0.f ? dp * rsqrtf(dp) * inv : 0.f);
+      }
+      const float4 rgbc = make_float4(g_a.col.x, g_a.col.y, g_a.col.z, fminf(lo2, kLog2AlphaMax));
       sl.sp0[lane] = make_float4(mu.x, mu.y, Lc.x, Lc.y);
       sl.sp1[lane] = make_float2(Lc.z, lo2);
 #pragma unroll
       for (int t = 0; t < TILES; ++t) {
         const int tx = gx * GW + (t % GW), ty = gy * GH + (t / GW);
         const bool active = valid && ((msk >> t) & 1u);
+        const uint32_t bal = __ballot_sync(0xffffffffu, active);
+        const uint32_t cnt_t = __popc(bal);
+        // active entries are packed to rows 0..cnt-1 in list order; the other lanes fill rows
+        // cnt..31 with a row whose exponent never passes the pruning test
+        const uint32_t pos = active ? __popc(bal & lt_mask) : cnt_t + __popc(~bal & lt_mask);
         bool scalar = false;
         uint4 r0 = make_uint4(0u, 0u, 0u, 0u), r1 = make_uint4(0u, 0u, 0u, 0u);
+        if (!active) r0.z = pack_h2(0.f, -30000.f);  // constant term of the padding rows
         if (active) {
           const float mx = mu.x - (float)(tx * kTile + 8), my = mu.y - (float)(ty * kTile + 8);
           // (u, v) = L m: the linear and constant terms are formed from it (conic m = L^T L m and
@@ -256,24 +355,26 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB, NPROD>::kThreads, 1)
                              8.f * (fabsf(q[3]) + fabsf(q[4])) + fabsf(q[5]);
           scalar = !(wsum <= kMaxWeightedCoef);
           if (!scalar) {
-            float hi[6], lo[6];
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-              hi[k] = __half2float(__float2half_rn(q[k]));
-              lo[k] = q[k] - hi[k];
-            }
-            r0.x = pack_h2(hi[0], hi[1]); r0.y = pack_h2(hi[2], hi[3]);
-            r0.z = pack_h2(hi[4], hi[5]); r0.w = pack_h2(lo[0], lo[1]);
-            r1.x = pack_h2(lo[2], lo[3]); r1.y = pack_h2(lo[4], lo[5]);
+            const __half2 h01 = __floats2half2_rn(q[0], q[1]), h23 = __floats2half2_rn(q[2], q[3]),
+                          h45 = __floats2half2_rn(q[4], q[5]);
+            const float2 f01 = __half22float2(h01), f23 = __half22float2(h23),
+                         f45 = __half22float2(h45);
+            r0.x = *reinterpret_cast<const uint32_t*>(&h01);
+            r0.y = *reinterpret_cast<const uint32_t*>(&h23);
+            r0.z = *reinterpret_cast<const uint32_t*>(&h45);
+            r0.w = pack_h2(q[0] - f01.x, q[1] - f01.y);
+            r1.x = pack_h2(q[2] - f23.x, q[3] - f23.y);
+            r1.y = pack_h2(q[4] - f45.x, q[5] - f45.y);
           }
+          sl.rgbc[t][pos] = rgbc;
+          sl.entry[t][pos] = (uint8_t)lane;
         }
-        uint8_t* rowp = &sl.B[t][(lane >> 3) * kSBO + (lane & 7) * 16];
+        uint8_t* rowp = &sl.B[t][(pos >> 3) * kSBO + (pos & 7) * 16];
         *reinterpret_cast<uint4*>(rowp) = r0;
         *reinterpret_cast<uint4*>(rowp + kLBO) = r1;
-        const uint32_t tb = __ballot_sync(0xffffffffu, active);
-        const uint32_t sb = __ballot_sync(0xffffffffu, active && scalar);
+        const uint32_t sb = __reduce_or_sync(0xffffffffu, (active && scalar) ? (1u << pos) : 0u);
         if (lane == 0) {
-          sl.tbits[t] = tb;
+          sl.cnt[t] = cnt_t;
           sl.sbits[t] = sb;
         }
       }
@@ -281,6 +382,13 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB, NPROD>::kThreads, 1)
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.full[s]);
+      // rotate the pipeline
+      g_a = g_b;
+      msk_a = msk_b;
+      val_a = val_b;
+      idx_b = idx_c;
+      msk_b = msk_c;
+      val_b = val_c;
     }
   } else if (warp == C::kMmaWarp) {
     // ---- MMA issuer ---------------------------------------------------------------------------
@@ -309,7 +417,7 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB, NPROD>::kThreads, 1)
 #pragma unroll
           for (int g = 0; g < NWG; ++g) {
             const int t = g + NWG * r;
-            if (sl.tbits[t] == 0u) continue;
+            if (sl.cnt[t] == 0u) continue;
             const uint64_t bdesc = smem_desc(smem_addr(&sl.B[t][0]), kLBO, kSBO);
             const uint32_t col = (uint32_t)(st * C::kStageCols + (2 * g) * NB);
             mma_f16(tmem + col, adesc0, bdesc, idesc, 0u);
@@ -340,7 +448,6 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB, NPROD>::kThreads, 1)
   } else {
     // ---- epilogue warpgroups ------------------------------------------------------------------
     const int wg = warp >> 2, quarter = warp & 3;
-    int px[C::kRounds][2], py[C::kRounds][2];
     PixState ps[C::kRounds][2];
     bool wdone[C::kRounds];
 #pragma unroll
@@ -352,10 +459,8 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB, NPROD>::kThreads, 1)
       for (int h = 0; h < 2; ++h) {
         int lx, ly;
         lane_pixel(h, quarter * 32 + lane, lx, ly);
-        px[r][h] = tx * kTile + lx;
-        py[r][h] = ty * kTile + ly;
-        const bool inside = px[r][h] < width && py[r][h] < height;
-        ps[r][h] = PixState{1.f, 0.f, 0.f, 0.f, 0, !inside};
+        const bool inside = tx * kTile + lx < width && ty * kTile + ly < height;
+        ps[r][h] = PixState{1.f, 0.f, 0.f, 0.f, inside ? kL255 : inf_f(), 0};
         all &= !inside;
       }
       wdone[r] = __all_sync(0xffffffffu, all);
@@ -376,51 +481,56 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB, NPROD>::kThreads, 1)
           break;
         }
         if (r == 0) {
-          // the slot's producer writes (colours, masks) are complete: the MMA thread waited on
+          // the slot's producer writes (colours, packing) are complete: the MMA thread waited on
           // the same phase before issuing this job
           ok = mbar_wait_bounded(&S.full[s], (c / SLOTS) & 1, abort_flag, kWaitLimitNs);
           if (!__all_sync(0xffffffffu, ok)) { record_abort(&S.abort, err); finished = true; break; }
         }
         ++job;
         tc_fence_after();
-        auto& sl = S.slot[s];
+        const auto& sl = S.slot[s];
         const int t = wg + NWG * r;
-        const uint32_t tb = sl.tbits[t];
-        const bool work = tb != 0u && !wdone[r];
+        const int cnt = (int)sl.cnt[t];
         const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) +
                                (uint32_t)(st * C::kStageCols + (2 * wg) * NB);
-        if (work) {
+        if (cnt > 0 && !wdone[r]) {
           const uint32_t sb = sl.sbits[t];
           const int base = sl.base;
-          // NB/16 halves of 16 columns; the stage is released after the last load
-#pragma unroll
-          for (int half = 0; half < NB / 16; ++half) {
-            float d0[16], d1[16];
-            __syncwarp();  // tcgen05.ld is warp-collective: reconverge after the blend branches
-            tmem_ld_2x16(taddr + half * 16, taddr + NB + half * 16, d0, d1);
-            if (half == NB / 16 - 1) {
+          const int tx = gx * GW + (t % GW), ty = gy * GH + (t / GW);
+          const int ngr = (cnt + 7) >> 3;  // 8-column granules holding the packed entries
+          uint32_t ga[16], gb[16];
+          __syncwarp();
+          tmem_ld8x2_async(taddr, taddr + NB, ga);
+          tmem_wait_ld(ga);
+          // granule g is blended while granule g + 1 is loading; the stage is released once its
+          // last load has completed
+          for (int g = 0; g < ngr; g += 2) {
+            if (g + 1 < ngr) {
+              __syncwarp();
+              tmem_ld8x2_async(taddr + 8 * (g + 1), taddr + NB + 8 * (g + 1), gb);
+            } else {
               tc_fence_before();
               __syncwarp();
               if (lane == 0) mbar_arrive(&S.tempty[st]);
             }
-#pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              const int j = half * 16 + jj;
-              if (!((tb >> j) & 1u)) continue;
-              const float4 rc = sl.rgbc[j];
-              float e0 = d0[jj], e1 = d1[jj];
-              if ((sb >> j) & 1u) {
-                const float4 p0 = sl.sp0[j];
-                const float2 p1 = sl.sp1[j];
-                e0 = scalar_exponent((float)px[r][0], (float)py[r][0], p0, p1);
-                e1 = scalar_exponent((float)px[r][1], (float)py[r][1], p0, p1);
+            blend_granule<TILES, COUNT>(ga, g, cnt, sb, base, sl, t, tx, ty, quarter, lane,
+                                        ps[r][0], ps[r][1], evaluated, passing);
+            if (g + 1 < ngr) {
+              tmem_wait_ld(gb);
+              if (g + 2 < ngr) {
+                __syncwarp();
+                tmem_ld8x2_async(taddr + 8 * (g + 2), taddr + NB + 8 * (g + 2), ga);
+              } else {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.tempty[st]);
               }
-              if (COUNT) evaluated += (!ps[r][0].done) + (!ps[r][1].done);
-              blend_step<COUNT>(e0, rc, ps[r][0], base + j + 1, passing);
-              blend_step<COUNT>(e1, rc, ps[r][1], base + j + 1, passing);
+              blend_granule<TILES, COUNT>(gb, g + 1, cnt, sb, base, sl, t, tx, ty, quarter, lane,
+                                          ps[r][0], ps[r][1], evaluated, passing);
+              if (g + 2 < ngr) tmem_wait_ld(ga);
             }
           }
-          wdone[r] = __all_sync(0xffffffffu, ps[r][0].done && ps[r][1].done);
+          wdone[r] = __all_sync(0xffffffffu, ps[r][0].thr == inf_f() && ps[r][1].thr == inf_f());
         } else {
           tc_fence_before();
           __syncwarp();
@@ -444,11 +554,16 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB, NPROD>::kThreads, 1)
     // ---- outputs ------------------------------------------------------------------------------
     const size_t HW = (size_t)width * height;
 #pragma unroll
-    for (int r = 0; r < C::kRounds; ++r)
+    for (int r = 0; r < C::kRounds; ++r) {
+      const int t = wg + NWG * r;
+      const int tx = gx * GW + (t % GW), ty = gy * GH + (t / GW);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        if (px[r][h] >= width || py[r][h] >= height) continue;
-        const size_t p = (size_t)py[r][h] * width + px[r][h];
+        int lx, ly;
+        lane_pixel(h, quarter * 32 + lane, lx, ly);
+        const int X = tx * kTile + lx, Y = ty * kTile + ly;
+        if (X >= width || Y >= height) continue;
+        const size_t p = (size_t)Y * width + X;
         const PixState& q = ps[r][h];
         out_rgb[p] = q.r + q.T * bg.x;
         out_rgb[HW + p] = q.g + q.T * bg.y;
@@ -456,6 +571,7 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB, NPROD>::kThreads, 1)
         out_T[p] = q.T;
         if (n_contrib) n_contrib[p] = q.last;
       }
+    }
     if (COUNT) {
       for (int o = 16; o > 0; o >>= 1) {
         evaluated += __shfl_xor_sync(0xffffffffu, evaluated, o);
@@ -475,12 +591,12 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NB, NPROD>::kThreads, 1)
   if (warp == C::kMmaWarp) tmem_dealloc(tmem, C::kTmemCols);
 }
 
-template <int GW, int GH, int NWG, int NB, int NPROD>
+template <int GW, int GH, int NWG, int NPROD>
 tgs_status launch_cfg(const tgs_projected& p, const tgs_bins& b, int width, int height,
                       const tgs_raster_opts& o, float* out_rgb, float* out_T, int32_t* n_contrib,
                       cudaStream_t st) {
-  using Cf = Cfg<GW, GH, NWG, NB, NPROD>;
-  using Sm = Smem<GW * GH, NB, Cf::kSlots>;
+  using Cf = Cfg<GW, GH, NWG, NPROD>;
+  using Sm = Smem<GW * GH, Cf::kSlots>;
   const int TX = div_up(width, kTile), TY = div_up(height, kTile);
   const int GX = div_up(TX, GW), GY = div_up(TY, GH);
   // Limit residency so that co-resident CTAs never wait on each other's tensor memory:
@@ -499,12 +615,12 @@ tgs_status launch_cfg(const tgs_projected& p, const tgs_bins& b, int width, int 
   const float3 bg = make_float3(o.bg[0], o.bg[1], o.bg[2]);
   int32_t* err = device_error_word();
   if (count) {
-    auto* k = k_raster_tc<GW, GH, NWG, NB, NPROD, true>;
+    auto* k = k_raster_tc<GW, GH, NWG, NPROD, true>;
     TGS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<GX * GY, Cf::kThreads, smem, st>>>(b.ranges, b.vals, b.masks, m2, co, p.rgb, width, height, GX,
                                            bg, out_rgb, out_T, n_contrib, cnt, err);
   } else {
-    auto* k = k_raster_tc<GW, GH, NWG, NB, NPROD, false>;
+    auto* k = k_raster_tc<GW, GH, NWG, NPROD, false>;
     TGS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<GX * GY, Cf::kThreads, smem, st>>>(b.ranges, b.vals, b.masks, m2, co, p.rgb, width, height, GX,
                                            bg, out_rgb, out_T, n_contrib, cnt, err);
@@ -520,11 +636,11 @@ tgs_status launch_raster_tc(const tgs_projected& p, const tgs_bins& b, int width
                             int32_t* n_contrib, cudaStream_t st) {
   if (((uintptr_t)p.mean2d & 7) || ((uintptr_t)p.conic_opacity & 15))
     return set_error("mean2d needs 8-byte and conic_opacity 16-byte alignment"), TGS_ERR_INVALID_ARGUMENT;
-  if (gw == 1 && gh == 1) return launch_cfg<1, 1, 1, 32, 2>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
-  if (gw == 2 && gh == 2) return launch_cfg<2, 2, 4, 32, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
-  if (gw == 4 && gh == 2) return launch_cfg<4, 2, 4, 32, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
-  if (gw == 2 && gh == 4) return launch_cfg<2, 4, 4, 32, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
-  if (gw == 4 && gh == 4) return launch_cfg<4, 4, 4, 32, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
+  if (gw == 1 && gh == 1) return launch_cfg<1, 1, 1, 2>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
+  if (gw == 2 && gh == 2) return launch_cfg<2, 2, 4, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
+  if (gw == 4 && gh == 2) return launch_cfg<4, 2, 4, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
+  if (gw == 2 && gh == 4) return launch_cfg<2, 4, 4, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
+  if (gw == 4 && gh == 4) return launch_cfg<4, 4, 4, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
   set_error("tensor-core path supports groups 1x1, 2x2, 4x2, 2x4, 4x4 (got %dx%d)", gw, gh);
   return TGS_ERR_INVALID_ARGUMENT;
 }
