@@ -143,6 +143,23 @@ tgs_status tgs_bin_sort(const tgs_projected* proj, int64_t n, int32_t width, int
                         const tgs_tiling* tiling, void* workspace, size_t workspace_bytes,
                         tgs_bins* bins, int64_t* num_entries_host, void* stream);
 
+/* Size of the fixed scratch area tgs_bin_sort_static uses (16 MiB). */
+#define TGS_BIN_SORT_STATIC_BYTES ((size_t)16 << 20)
+
+/* tgs_bin_sort without a caller workspace and without any device allocation. The paper has no
+ * counterpart: this serves callers that cannot allocate device memory while they run (a real-time
+ * frame loop or compositor with a memory budget fixed at start-up, or a host application that owns
+ * every device allocation). The scratch is a fixed TGS_BIN_SORT_STATIC_BYTES array inside the
+ * library, held by every GPU that loads it until the process exits. Same arguments, outputs and
+ * errors as tgs_bin_sort, plus TGS_ERR_CAPACITY (with a message) when
+ * tgs_bin_sort_workspace_size(n, bins->capacity, ...) exceeds TGS_BIN_SORT_STATIC_BYTES (e.g.
+ * about 130k Gaussians with 1M entries). The first call on a device resolves the array's device
+ * address (cudaGetSymbolAddress) and must come before any stream capture on that device. All
+ * calls share the array; calls that overlap on the GPU (other streams or host threads) race. */
+tgs_status tgs_bin_sort_static(const tgs_projected* proj, int64_t n, int32_t width, int32_t height,
+                               const tgs_tiling* tiling, tgs_bins* bins, int64_t* num_entries_host,
+                               void* stream);
+
 /* Rasterize (Section 2 Eqs. power_d..blend; Section 4.2 tensorization; Section 4.4.2 grouping).
  * One CTA per tile group walks the group's sorted list in chunks; per pixel, in list order,
  * entries whose mask bit for the pixel's tile is set: power = -1/2 d^T conic d with d = x - mu';

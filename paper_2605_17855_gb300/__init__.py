@@ -83,6 +83,8 @@ SIGNATURES = {
                                                 C.POINTER(_Tiling), C.POINTER(C.c_size_t)]),
     "tgs_bin_sort": (C.c_int32, [C.POINTER(_Projected), C.c_int64, C.c_int32, C.c_int32, C.POINTER(_Tiling),
                                  _P, C.c_size_t, C.POINTER(_Bins), C.POINTER(C.c_int64), _P]),
+    "tgs_bin_sort_static": (C.c_int32, [C.POINTER(_Projected), C.c_int64, C.c_int32, C.c_int32,
+                                        C.POINTER(_Tiling), C.POINTER(_Bins), C.POINTER(C.c_int64), _P]),
     "tgs_rasterize": (C.c_int32, [C.POINTER(_Projected), C.c_int64, C.POINTER(_Bins), C.c_int32, C.c_int32,
                                   C.POINTER(_Tiling), C.POINTER(_RasterOpts), _P, _P, _P, _P]),
     "tgs_rasterize_backward": (C.c_int32, [C.POINTER(_Projected), C.c_int64, C.POINTER(_Bins), C.c_int32,
@@ -287,6 +289,20 @@ def bin_sort(proj: Projected, width, height, tiling=(2, 2), bins: Bins | None = 
         if sync:
             bins.entries = int(host.value)
         return bins
+
+
+def bin_sort_static(proj: Projected, width, height, bins: Bins, sync=True, stream=None) -> Bins:
+    """tgs_bin_sort_static: the bin sort using the library's fixed scratch area instead of
+    bins.workspace (for callers that must not allocate device memory). `bins` must already be
+    allocated with enough capacity."""
+    lib = load()
+    t = _tiling(bins.tiling)
+    host = C.c_int64(0)
+    _check(lib.tgs_bin_sort_static(C.byref(proj.struct()), proj.n, int(width), int(height), C.byref(t),
+                                   C.byref(bins.struct()), C.byref(host) if sync else None, _stream(stream)))
+    if sync:
+        bins.entries = int(host.value)
+    return bins
 
 
 # ------------------------------------------------------------------------------------------------

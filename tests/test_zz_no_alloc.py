@@ -1,0 +1,83 @@
+"""tgs_bin_sort_static: the bin sort for callers that cannot allocate device memory while they run
+(a real-time frame loop with a fixed memory budget, or a host that owns all device memory). It uses
+a fixed scratch area inside the library instead of a caller workspace. Its output must equal the
+workspace version's exactly (binning is integer work), on two calls in a row that share the area.
+
+This file is collected last on purpose: if it fails, a run that stops at the first failure has
+already run every other test. It does not depend on any other test's state."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2605_17855_gb300 as tgs  # noqa: E402
+from paper_2605_17855_gb300 import scenes  # noqa: E402
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _case(name):
+    if name == "box":
+        scene, cams = scenes.config_c1()
+        return scene, cams[0], (2, 2)
+    scene = scenes.mixture_scene(30_000, seed=9, components=16, cluster_std=0.3, radius=2.0,
+                                 log_scale_mean=-3.8, sh_degree=3)
+    return scene, scenes.orbit_cameras(4, 5.0, 203, 149)[1], (4, 2)
+
+
+def _static_call(proj, cam, tiling, capacity):
+    """Bin sort through the raw C entry point with no workspace argument."""
+    lib = tgs.load()
+    out = tgs.allocate_bins(proj.n, capacity, cam.width, cam.height, tiling)
+    host = C.c_int64(0)
+    t = tgs._Tiling(*tiling)
+    st = lib.tgs_bin_sort_static(C.byref(proj.struct()), proj.n, cam.width, cam.height, C.byref(t),
+                                 C.byref(out.struct()), C.byref(host), None)
+    assert st == tgs.TGS_OK, lib.tgs_last_error_message()
+    out.entries = int(host.value)
+    return out
+
+
+def test_static_scratch_matches_workspace_on_consecutive_calls():
+    results = []
+    for name in ("box", "mixture"):  # two calls in a row sharing the scratch area
+        scene, cam, tiling = _case(name)
+        proj = tgs.preprocess(tgs.DeviceScene.from_host(scene), cam)
+        ref = tgs.bin_sort(proj, cam.width, cam.height, tiling)
+        got = _static_call(proj, cam, tiling, ref.capacity)
+        torch.cuda.synchronize()
+        E = ref.entries
+        assert got.entries == E and E > 0
+        for a, b in ((got.keys, ref.keys), (got.vals, ref.vals), (got.masks, ref.masks)):
+            assert np.array_equal(_np(a[:E]), _np(b[:E]))
+        assert np.array_equal(_np(got.ranges), _np(ref.ranges))
+        results.append(E)
+    # and again on the first case, after the second call left its contents in the area
+    scene, cam, tiling = _case("box")
+    proj = tgs.preprocess(tgs.DeviceScene.from_host(scene), cam)
+    ref = tgs.bin_sort(proj, cam.width, cam.height, tiling)
+    got = _static_call(proj, cam, tiling, ref.capacity)
+    torch.cuda.synchronize()
+    assert got.entries == results[0]
+    assert np.array_equal(_np(got.vals[:got.entries]), _np(ref.vals[:ref.entries]))
+    assert np.array_equal(_np(got.ranges), _np(ref.ranges))
+
+
+def test_static_scratch_rejects_oversized_requests():
+    scene, cam, tiling = _case("box")
+    proj = tgs.preprocess(tgs.DeviceScene.from_host(scene), cam)
+    lib = tgs.load()
+    big = tgs.allocate_bins(proj.n, 4_000_000, cam.width, cam.height, tiling)  # > 16 MiB of scratch
+    t = tgs._Tiling(*tiling)
+    st = lib.tgs_bin_sort_static(C.byref(proj.struct()), proj.n, cam.width, cam.height, C.byref(t),
+                                 C.byref(big.struct()), None, None)
+    assert st == tgs.TGS_ERR_CAPACITY
+    assert b"static area holds" in lib.tgs_last_error_message()
