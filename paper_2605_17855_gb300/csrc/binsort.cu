@@ -21,8 +21,8 @@ namespace {
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kSortThreads = 256;  // 8 warps
-constexpr int kSortItems = 8;      // per thread
-constexpr int kSortTile = kSortThreads * kSortItems;  // 2048 items per block
+constexpr int kSortItems = 16;     // per thread
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 items per block
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
@@ -146,14 +146,21 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
     hist[(int64_t)d * num_blocks + blockIdx.x] = h[d];
 }
 
+// Stable scatter of one pass. Each warp ranks its 256 consecutive items by digit (match_any),
+// warps are ordered, so the block's items get their stable position in digit order; they are staged
+// in shared memory in that order and written out so that each digit's run is contiguous and the
+// global stores of consecutive threads are consecutive.
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const int64_t* count_dev,
     int64_t count_host, int64_t cap, int shift, const uint32_t* __restrict__ offsets,
     int num_blocks) {
   constexpr int W = kSortThreads / 32;
-  __shared__ uint32_t wcount[W][kRadix];
-  __shared__ uint32_t boff[kRadix];
+  __shared__ uint32_t wcount[W][kRadix];  // per warp and digit: count, then exclusive offset
+  __shared__ uint32_t dstart[kRadix];     // block-local start of each digit's run
+  __shared__ uint32_t boff[kRadix];       // global start of this block's run of each digit
+  __shared__ uint32_t warp_tot[kRadix / 32];
+  __shared__ uint32_t skey[kSortTile], sval[kSortTile];
   const int64_t count = live_count(count_dev, count_host, cap);
   const int64_t block_base = (int64_t)blockIdx.x * kSortTile;
   if (block_base >= count) return;  // uniform per block
@@ -181,25 +188,52 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     rank[r] = base + before;
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
-    uint32_t run = 0;
+  // per digit: exclusive offsets over warps and the block total; then an exclusive scan of the
+  // totals over digits (one thread per digit)
+  static_assert(kSortThreads >= kRadix, "one thread per digit");
+  uint32_t total = 0;
+  if (threadIdx.x < kRadix) {
+    const int d = threadIdx.x;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
       const uint32_t c = wcount[w][d];
-      wcount[w][d] = run;
-      run += c;
+      wcount[w][d] = total;
+      total += c;
     }
     boff[d] = offsets[(int64_t)d * num_blocks + blockIdx.x];
+    uint32_t incl = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    total = incl - total;  // exclusive within the warp
+  }
+  __syncthreads();
+  if (threadIdx.x < kRadix) {
+    uint32_t add = 0;
+    for (int w = 0; w < warp; ++w) add += warp_tot[w];
+    dstart[threadIdx.x] = total + add;
   }
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     const int d = dig[r];
     if (d < kRadix) {
-      const uint32_t pos = boff[d] + wcount[warp][d] + rank[r];
-      keys_out[pos] = key[r];
-      vals_out[pos] = val[r];
+      const uint32_t p = dstart[d] + wcount[warp][d] + rank[r];
+      skey[p] = key[r];
+      sval[p] = val[r];
     }
+  }
+  __syncthreads();
+  const int nvalid = (int)min((int64_t)kSortTile, count - block_base);
+  for (int i = threadIdx.x; i < nvalid; i += kSortThreads) {
+    const uint32_t k = skey[i];
+    const int d = (int)((k >> shift) & (kRadix - 1));
+    const uint32_t pos = boff[d] + (uint32_t)i - dstart[d];
+    keys_out[pos] = k;
+    vals_out[pos] = sval[i];
   }
 }
 
@@ -257,24 +291,62 @@ __global__ void k_group_counts(int n, const uint32_t* __restrict__ order,
   counts[s] = c;
 }
 
-__global__ void k_emit(int n, const uint32_t* __restrict__ order, const int* __restrict__ radius,
-                       const int4* __restrict__ rect, const uint64_t* __restrict__ offsets,
-                       const int64_t* __restrict__ total, int64_t cap, int gw, int gh, int GX,
-                       uint32_t* __restrict__ gkeys, uint32_t* __restrict__ vals) {
+// Duplicates each visible Gaussian once per overlapped group, in depth order. A warp handles 32
+// consecutive Gaussians; their entries are contiguous in the output, so the warp writes them
+// cooperatively (lane k of a round writes entry k), each lane locating its Gaussian by a binary
+// search over the warp's prefix of counts.
+__global__ void __launch_bounds__(256) k_emit(int n, const uint32_t* __restrict__ order,
+                                              const int* __restrict__ radius,
+                                              const int4* __restrict__ rect,
+                                              const uint64_t* __restrict__ offsets,
+                                              const int64_t* __restrict__ total, int64_t cap,
+                                              int gw, int gh, int GX, uint32_t* __restrict__ gkeys,
+                                              uint32_t* __restrict__ vals) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const int64_t E = *total;
-  if (E > cap) return;
-  const uint32_t i = order[s];
-  if (radius[i] <= 0) return;
-  const int4 r = rect[i];
-  uint64_t o = offsets[s];
-  for (int gy = r.y / gh; gy <= (r.w - 1) / gh; ++gy)
-    for (int gx = r.x / gw; gx <= (r.z - 1) / gw; ++gx) {
-      gkeys[o] = (uint32_t)(gy * GX + gx);
-      vals[o] = i;
-      ++o;
+  const int lane = threadIdx.x & 31;
+  if (*total > cap) return;
+  if ((s - lane) >= n) return;  // the whole warp is past the end
+  uint32_t i = 0, cnt = 0;
+  int gx0 = 0, gy0 = 0, gwn = 1;
+  if (s < n) {
+    i = order[s];
+    if (radius[i] > 0) {
+      const int4 r = rect[i];
+      gx0 = r.x / gw;
+      gy0 = r.y / gh;
+      gwn = (r.z - 1) / gw - gx0 + 1;
+      cnt = (uint32_t)(gwn * ((r.w - 1) / gh - gy0 + 1));
     }
+  }
+  // inclusive prefix of the counts over the warp
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  const uint32_t warp_total = __shfl_sync(0xffffffffu, incl, 31);
+  const uint64_t base = __shfl_sync(0xffffffffu, (s < n) ? offsets[s] : 0ull, 0);
+  for (uint32_t k0 = 0; k0 < warp_total; k0 += 32) {
+    const uint32_t k = k0 + lane;
+    // smallest source lane whose inclusive prefix exceeds k
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const uint32_t v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+      if (v <= k) lo += step;
+    }
+    const uint32_t src_excl = __shfl_sync(0xffffffffu, incl - cnt, lo);
+    const uint32_t src_i = __shfl_sync(0xffffffffu, i, lo);
+    const int sx = __shfl_sync(0xffffffffu, gx0, lo), sy = __shfl_sync(0xffffffffu, gy0, lo);
+    const int sw = __shfl_sync(0xffffffffu, gwn, lo);
+    if (k < warp_total) {
+      const int li = (int)(k - src_excl);
+      const uint64_t o = base + k;
+      gkeys[o] = (uint32_t)((sy + li / sw) * GX + (sx + li % sw));
+      vals[o] = src_i;
+    }
+  }
 }
 
 __global__ void k_finalize(const int64_t* __restrict__ total, int64_t cap,
@@ -394,8 +466,8 @@ tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int h
   uint32_t* ev = (passes & 1) ? gvB : b.vals;
   uint32_t* ok = (passes & 1) ? gkA : gkB;
   uint32_t* ov = (passes & 1) ? b.vals : gvB;
-  k_emit<<<div_up(n, threads), threads, 0, st>>>(n, order, p.radius, rect, counts, b.num_entries, cap,
-                                                 gw, gh, GX, ek, ev);
+  k_emit<<<div_up(n, 256), 256, 0, st>>>(n, order, p.radius, rect, counts, b.num_entries, cap, gw, gh,
+                                          GX, ek, ev);
   TGS_CHECK_LAUNCH("k_emit");
 
   // 4. stable sort by group id

@@ -57,7 +57,7 @@ __device__ void cov2d_f32(const CamParams& c, float3 pc, float4 q, float3 s, flo
 }
 
 // Same quantity in FP64 from the same FP32 inputs (used only for near-degenerate splats).
-__device__ void cov2d_f64(const CamParams& c, const float* m, float4 qf, float3 s, double& cxx,
+__device__ __noinline__ void cov2d_f64(const CamParams& c, const float* m, float4 qf, float3 s, double& cxx,
                           double& cxy, double& cyy) {
   double pc[3];
 #pragma unroll
@@ -95,9 +95,8 @@ __device__ void cov2d_f64(const CamParams& c, const float* m, float4 qf, float3 
 
 // Real SH basis up to degree 3 (index l*l + m + l), Condon-Shortley phase kept in the real form.
 template <int DEG>
-__device__ __forceinline__ float3 sh_colour(const float* shp, float3 d) {
+__device__ __forceinline__ void sh_basis(float3 d, float (&Y)[16]) {
   const float x = d.x, y = d.y, z = d.z;
-  float Y[16];
   Y[0] = 0.28209479177387814f;
   if (DEG >= 1) {
     const float k1 = 0.4886025119029199f;
@@ -120,16 +119,33 @@ __device__ __forceinline__ float3 sh_colour(const float* shp, float3 d) {
       Y[15] = -k3a * x * (xx - 3.f * yy);
     }
   }
+}
+
+// Colour = sum_k sh[k] Y_k(d) + 0.5, clamped at 0. The coefficients are streamed (16-byte loads
+// when the per-Gaussian block is a multiple of 16 bytes) and accumulated as they arrive.
+template <int DEG>
+__device__ __forceinline__ float3 sh_colour(const float* __restrict__ sp, float3 d) {
   constexpr int NC = (DEG + 1) * (DEG + 1);
-  float3 col = make_float3(0.5f, 0.5f, 0.5f);
+  float Y[16];
+  sh_basis<DEG>(d, Y);
+  float acc[3] = {0.5f, 0.5f, 0.5f};
+  if constexpr ((3 * NC) % 4 == 0) {
+    const float4* sp4 = reinterpret_cast<const float4*>(sp);
 #pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    col.x += shp[3 * k] * Y[k];
-    col.y += shp[3 * k + 1] * Y[k];
-    col.z += shp[3 * k + 2] * Y[k];
+    for (int k = 0; k < 3 * NC / 4; ++k) {
+      const float4 v = __ldg(sp4 + k);
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int f = 4 * k + q;  // flattened (coefficient, channel)
+        acc[f % 3] = fmaf(vv[q], Y[f / 3], acc[f % 3]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int f = 0; f < 3 * NC; ++f) acc[f % 3] = fmaf(__ldg(sp + f), Y[f / 3], acc[f % 3]);
   }
-  col.x = fmaxf(col.x, 0.f); col.y = fmaxf(col.y, 0.f); col.z = fmaxf(col.z, 0.f);
-  return col;
+  return make_float3(fmaxf(acc[0], 0.f), fmaxf(acc[1], 0.f), fmaxf(acc[2], 0.f));
 }
 
 __device__ __forceinline__ int64_t floor_div_tile(int64_t v) {
@@ -137,7 +153,7 @@ __device__ __forceinline__ int64_t floor_div_tile(int64_t v) {
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(256) k_preprocess(int n, const float* __restrict__ means,
+__global__ void __launch_bounds__(256, 4) k_preprocess(int n, const float* __restrict__ means,
                                                     const float* __restrict__ scales,
                                                     const float4* __restrict__ quats,
                                                     const float* __restrict__ opac,
@@ -210,30 +226,18 @@ __global__ void __launch_bounds__(256) k_preprocess(int n, const float* __restri
         const float inv = 1.f / sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
         d.x *= inv; d.y *= inv; d.z *= inv;
         constexpr int NC = (DEG + 1) * (DEG + 1);
-        float shv[3 * NC];
-        const float* sp = sh + (int64_t)i * 3 * NC;
-        if constexpr ((3 * NC) % 4 == 0) {
-          const float4* sp4 = reinterpret_cast<const float4*>(sp);
-#pragma unroll
-          for (int k = 0; k < 3 * NC / 4; ++k) {
-            const float4 v = __ldg(sp4 + k);
-            shv[4 * k] = v.x; shv[4 * k + 1] = v.y; shv[4 * k + 2] = v.z; shv[4 * k + 3] = v.w;
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < 3 * NC; ++k) shv[k] = __ldg(sp + k);
-        }
-        o_rgb = sh_colour<DEG>(shv, d);
+        o_rgb = sh_colour<DEG>(sh + (int64_t)i * 3 * NC, d);
       }
     }
   }
+  radius[i] = o_r;
+  if (o_r == 0) return;  // culled: no consumer reads the other outputs of this Gaussian
   mean2d[i] = o_mean;
   conic_opacity[i] = o_co;
   rgb[3 * i] = o_rgb.x;
   rgb[3 * i + 1] = o_rgb.y;
   rgb[3 * i + 2] = o_rgb.z;
   depth[i] = o_depth;
-  radius[i] = o_r;
   rect[i] = o_rect;
 }
 
