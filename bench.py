@@ -239,100 +239,87 @@ def main():
     scene, cams = scenes.config_c2(n=args.splats)
     H, W = cams[0].height, cams[0].width
     ds = tgs.DeviceScene.from_host(scene)
-    proj = tgs.Projected.empty(scene.n)
-    # size one bin buffer for the largest camera frame (one synchronous count per camera)
-    cap, cap32 = 0, 0
-    for cam in cams:
-        tgs.preprocess(ds, cam, out=proj)
-        cap = max(cap, tgs.bin_sort(proj, W, H, tiling).entries)
-        cap32 = max(cap32, tgs.bin_sort(proj, W, H, (1, 1)).entries)
-    bins = tgs.allocate_bins(scene.n, int(cap * 1.05) + 4096, W, H, tiling, keys=False)
-    bins32 = tgs.allocate_bins(scene.n, int(cap32 * 1.05) + 4096, W, H, (1, 1), keys=False)
-    imgs = [(torch.empty((3, H, W), device="cuda"), torch.empty((H, W), device="cuda")) for _ in cams]
     stream = torch.cuda.current_stream()
+    # one pair of CUDA graphs per camera (preprocess + bin sort, rasterize): a frame is two launches
+    rend = tgs.Renderer(ds, cams, tiling, args.precision)
+    rend32 = tgs.Renderer(ds, cams, (1, 1), "fp32")  # the plain tile rasterizer, 1x1 tiles
+    # ablation: the same tensor-core path without the exact (Gaussian, tile) skip
+    rend_nc = tgs.Renderer(ds, cams, tiling, args.precision, cull=False) if args.precision == "fp16_tc" else None
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
-    def frame(cam, out, prec, bn, til_events=None):
-        tgs.preprocess(ds, cam, out=proj)
-        tgs.bin_sort(proj, W, H, bn.tiling, bins=bn, sync=False)
-        if til_events is not None:
-            til_events[0].record(stream)
-        tgs.rasterize(proj, bn, W, H, prec, out=(out[0], out[1], None), want_n_contrib=False)
-        if til_events is not None:
-            til_events[1].record(stream)
-
-    def step(prec, bn, frame_events=None, raster_events=None):
-        for i, cam in enumerate(cams):
-            if frame_events is not None:
-                frame_events[i][0].record(stream)
-            frame(cam, imgs[i], prec, bn, raster_events[i] if raster_events is not None else None)
-            if frame_events is not None:
-                frame_events[i][1].record(stream)
-
-    def timed(prec, bn, steps, warmup):
+    def timed(r, steps, warmup):
         for _ in range(warmup):
-            step(prec, bn)
+            for i in range(len(cams)):
+                r.render(i)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-        fr = [[(ev(), ev()) for _ in cams] for _ in range(steps)]
-        rs = [[(ev(), ev()) for _ in cams] for _ in range(steps)]
-        launches0 = tgs.kernel_launch_count()
+        evs = [[(ev(), ev(), ev()) for _ in cams] for _ in range(steps)]
         t0, t1 = ev(), ev()
         t0.record(stream)
         for k in range(steps):
-            step(prec, bn, fr[k], rs[k])
+            for i in range(len(cams)):
+                r.render(i, evs[k][i])
         t1.record(stream)
         torch.cuda.synchronize()
-        launches = tgs.kernel_launch_count() - launches0
         total_ms = t0.elapsed_time(t1)
         if dist:
             tt = torch.tensor([total_ms], device="cuda")
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             total_ms = float(tt.item())
             dist.barrier()
-        frames = np.array([a.elapsed_time(b) for row in fr for a, b in row])
-        raster = np.array([a.elapsed_time(b) for row in rs for a, b in row])
-        return total_ms, frames, raster, launches
+        frames = np.array([a.elapsed_time(c) for row in evs for a, _, c in row])
+        prep = np.array([a.elapsed_time(m) for row in evs for a, m, _ in row])
+        raster = np.array([m.elapsed_time(c) for row in evs for _, m, c in row])
+        return total_ms, frames, prep, raster
 
     sampler = ClockSampler(local)
     sampler.start()
-    total_ms, frames_ms, raster_ms, launches = timed(args.precision, bins, args.steps, args.warmup)
+    total_ms, frames_ms, prep_ms, raster_ms = timed(rend, args.steps, args.warmup)
     clocks = sampler.stop()
+    launches = int(args.steps * sum(rend.kernels_per_frame))
     ms_per_step = total_ms / args.steps
     px_per_step = len(cams) * W * H
     value = ws * px_per_step / (ms_per_step * 1e-3) / 1e6
-    # FP32 CUDA-core rasterizer, 1x1 tiles: the plain tile rasterizer, same scene and GPU
-    tot32, frames32, raster32, _ = timed("fp32", bins32, max(2, args.steps // 2), 3)
-    value32 = ws * px_per_step / (tot32 / max(2, args.steps // 2) * 1e-3) / 1e6
+    steps32 = max(3, args.steps // 2)
+    tot32, frames32, prep32, raster32 = timed(rend32, steps32, 3)
+    value32 = ws * px_per_step / (tot32 / steps32 * 1e-3) / 1e6
+    ablation = None
+    if rend_nc is not None:
+        totnc, framesnc, _, rasternc = timed(rend_nc, steps32, 3)
+        ablation = {"value": round(ws * px_per_step / (totnc / steps32 * 1e-3) / 1e6, 3), "unit": UNIT,
+                    "rasterize_ms_mean": round(float(rasternc.mean()), 4),
+                    "note": "fp16_tc without the exact per-(Gaussian, tile) skip (identical images)"}
+    if rend.overflowed() or rend32.overflowed():
+        raise RuntimeError("bin capacity overflow during the benchmark")
 
-    # per-stage split of one frame (untimed by the main loop)
-    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    e = [ev() for _ in range(4)]
+    # split of the preprocess + bin sort stage for one frame (direct calls, untimed by the main loop)
+    e = [ev() for _ in range(3)]
     e[0].record(stream)
-    tgs.preprocess(ds, cams[0], out=proj)
+    tgs.preprocess(ds, cams[0], out=rend.proj)
     e[1].record(stream)
-    tgs.bin_sort(proj, W, H, tiling, bins=bins, sync=False)
+    tgs.bin_sort(rend.proj, W, H, tiling, bins=rend.bins, sync=False)
     e[2].record(stream)
-    tgs.rasterize(proj, bins, W, H, args.precision, out=(imgs[0][0], imgs[0][1], None), want_n_contrib=False)
-    e[3].record(stream)
     torch.cuda.synchronize()
-    stages = {"preprocess_ms": round(e[0].elapsed_time(e[1]), 4), "bin_sort_ms": round(e[1].elapsed_time(e[2]), 4),
-              "rasterize_ms": round(e[2].elapsed_time(e[3]), 4)}
+    stages = {"preprocess_plus_bin_sort_ms": round(float(prep_ms.mean()), 4),
+              "rasterize_ms": round(float(raster_ms.mean()), 4),
+              "preprocess_ms_direct": round(e[0].elapsed_time(e[1]), 4),
+              "bin_sort_ms_direct": round(e[1].elapsed_time(e[2]), 4)}
 
     # algorithmic work of the dominant kernel: evaluated pairs and exponentials per launch
     cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
-    for cam in cams:
-        tgs.preprocess(ds, cam, out=proj)
-        tgs.bin_sort(proj, W, H, tiling, bins=bins, sync=False)
-        tgs.rasterize(proj, bins, W, H, args.precision, out=(imgs[0][0], imgs[0][1], None),
+    for i, cam in enumerate(cams):
+        tgs.preprocess(ds, cam, out=rend.proj)
+        tgs.bin_sort(rend.proj, W, H, tiling, bins=rend.bins, sync=False)
+        tgs.rasterize(rend.proj, rend.bins, W, H, args.precision, out=(rend.out[i][0], rend.out[i][1], None),
                       want_n_contrib=False, counters=cnt)
     torch.cuda.synchronize()
     pairs, exps = [int(v) / len(cams) for v in cnt.cpu().tolist()]
-    entries = int(bins.num_entries.item())
+    entries = int(rend.bins.num_entries.item())
 
-    # end to end through the public API: scene H2D from pinned memory, 8 images D2H to pinned memory
+    # end to end through the public API: the scene copied host -> device from pinned memory and
+    # the 8 images device -> host into pinned memory, every step
     host = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32)).pin_memory()
             for k in ("means", "scales", "quats", "opacities", "sh")}
     host_imgs = [torch.empty((3, H, W), dtype=torch.float32).pin_memory() for _ in cams]
@@ -342,14 +329,14 @@ def main():
     def e2e_step():
         for k, t in host.items():
             getattr(ds, k).copy_(t, non_blocking=True)
-        for i, cam in enumerate(cams):
-            frame(cam, imgs[i], args.precision, bins)
-            host_imgs[i].copy_(imgs[i][0], non_blocking=True)
+        for i in range(len(cams)):
+            rgb, _ = rend.render(i)
+            host_imgs[i].copy_(rgb, non_blocking=True)
 
     for _ in range(2):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_steps = max(2, args.steps // 2)
+    e2e_steps = max(3, args.steps // 2)
     a, b = ev(), ev()
     a.record(stream)
     for _ in range(e2e_steps):
@@ -388,21 +375,26 @@ def main():
            "fps": round(1000.0 / float(frames_ms.mean()), 2),
            "fp32_core_1x1": {"value": round(value32, 3), "unit": UNIT,
                              "frame_ms_p99": round(float(np.percentile(frames32, 99)), 4),
+                             "preprocess_plus_bin_sort_ms": round(float(prep32.mean()), 4),
                              "rasterize_ms_mean": round(float(raster32.mean()), 4)},
+           "fp16_tc_without_tile_skip": ablation,
            "speedup_vs_fp32_core": round(value / value32, 3),
            "rasterize_speedup_vs_fp32_core": round(float(raster32.mean()) / raster_avg_ms, 3),
            "stages": stages,
            "evals_per_s": round(pairs * len(cams) / (ms_per_step * 1e-3), 1),
            "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4)},
-           "gpu_launches": int(launches),
+           "gpu_launches": launches,
+           "kernels_per_frame": rend.kernels_per_frame[0],
+           "graphs": "one CUDA graph pair per camera (preprocess + bin sort, rasterize)",
            "clocks": clocks,
            "roofline": roofline}
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        tgs.preprocess(ds, cams[0], out=proj)
-        tgs.bin_sort(proj, W, H, tiling, bins=bins, sync=False)
-        rgb, _, _ = tgs.rasterize(proj, bins, W, H, args.precision, want_n_contrib=False)
+        for k, t in host.items():  # restore the scene (the e2e loop copied the same values back)
+            getattr(ds, k).copy_(t)
+        rgb, _ = rend.render(0)
+        torch.cuda.synchronize()
         rec, psnr = cpu_baseline(scene, cams[0], tc_image=rgb.cpu().numpy(), target_s=args.cpu_sample_s)
         out["cpu_baseline"] = rec
         out["psnr_vs_oracle_sampled"] = round(psnr, 3) if psnr is not None and math.isfinite(psnr) else psnr

@@ -86,7 +86,8 @@ typedef struct {
   float* conic_opacity; /* [n,4] (a, b, c, o): inverse projected covariance [[a,b],[b,c]], opacity */
   float* rgb;           /* [n,3] SH colour, clamped at 0 */
   float* depth;         /* [n]   camera-space z */
-  int32_t* radius;      /* [n]   ceil(3 sqrt(lambda_max)) in pixels; 0 = culled */
+  int32_t* radius;      /* [n]   ceil(3 sqrt(lambda_max)) in pixels; 0 = culled (then the other
+                           arrays of that Gaussian are not written) */
   int32_t* rect;        /* [n,4] overlapped tile range (tx0, ty0, tx1, ty1), max exclusive */
 } tgs_projected;
 
@@ -100,12 +101,19 @@ typedef struct {
   int64_t* num_entries; /* device scalar: entries needed by this frame (may exceed capacity) */
 } tgs_bins;
 
+/* Flags of tgs_raster_opts. */
+#define TGS_RASTER_NO_CULL 1 /* FP16_TC: do not skip (Gaussian, tile) pairs whose exponent cannot
+                                reach log2(1/255) anywhere in the tile (the skip never changes the
+                                image; this flag exists to measure it) */
+
 typedef struct {
   int32_t precision;    /* TGS_PRECISION_* */
+  int32_t flags;        /* TGS_RASTER_* */
   float bg[3];          /* background colour added as T_final * bg */
-  int64_t* counters;    /* optional device [2] int64, accumulated: [0] evaluated (pixel, entry)
-                           pairs before termination (mask bit set), [1] of those, the pairs with
-                           alpha >= 1/255 (each needs one exp); NULL = not counted */
+  int64_t* counters;    /* optional device [2] int64, accumulated: [0] (pixel, entry) pairs
+                           evaluated before termination (mask bit set; FP16_TC does not count the
+                           pairs of a tile it skipped as provably below 1/255), [1] of those, the
+                           pairs with alpha >= 1/255 (each needs one exp); NULL = not counted */
 } tgs_raster_opts;
 
 /* ---------------------------------------------------------------------------------------------- */
@@ -122,7 +130,8 @@ tgs_status tgs_check_device(int32_t device);
  * Jacobian taken at x/z, y/z clamped to +-1.3 tan(half FOV); 2D covariance + 0.3 I; conic = its
  * inverse (near-degenerate covariances, det < 2^-5 Sxx Syy, are recomputed in FP64); radius =
  * ceil(3 sqrt(lambda_max)); tile range of the AABB [mu'-r, mu'+r]^2 (tiles holding an image pixel
- * inside it; empty -> culled); SH colour + 0.5 clamped at 0. Culled entries get radius 0.
+ * inside it; empty -> culled); SH colour + 0.5 clamped at 0. A culled Gaussian gets radius 0 and
+ * its other outputs are left unwritten (no call reads them).
  * Errors: INVALID_ARGUMENT for NULL pointers with n > 0, n < 0, sh_degree outside 0..3, bad camera. */
 tgs_status tgs_preprocess(const tgs_scene* scene, const tgs_camera* cam, tgs_projected* out,
                           void* stream);
@@ -167,7 +176,9 @@ tgs_status tgs_bin_sort_static(const tgs_projected* proj, int64_t n, int32_t wid
  * pixel stops without blending this entry; else C += alpha T rgb, T = T'.
  * FP16_TC evaluates log2(o) + log2(e) power as a product of pixel features [x^2, xy, y^2, x, y, 1]
  * (relative to the tile centre, exact in FP16) with per-Gaussian coefficients split hi + lo in FP16,
- * padded to K = 16, accumulated in FP32 in tensor memory; exp and blending are FP32.
+ * padded to K = 16, accumulated in FP32 in tensor memory; exp and blending are FP32. It skips a
+ * (Gaussian, tile) pair when the exact maximum of the exponent over the tile's pixels is below
+ * log2(1/255) by a margin (unless TGS_RASTER_NO_CULL): such a pair is pruned at every pixel anyway.
  * Outputs (device, caller-allocated): out_rgb [3,H,W] = C + T bg; out_T [H,W] = final T;
  * n_contrib [H,W] = 1-based position in the group list of the last blended entry (0 = none), may be
  * NULL. Errors: INVALID_ARGUMENT for bad sizes/tiling/precision; UNSUPPORTED_DEVICE for FP16_TC on a

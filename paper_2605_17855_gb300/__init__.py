@@ -65,7 +65,11 @@ class _Bins(C.Structure):
 
 
 class _RasterOpts(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("bg", C.c_float * 3), ("counters", C.c_void_p)]
+    _fields_ = [("precision", C.c_int32), ("flags", C.c_int32), ("bg", C.c_float * 3),
+                ("counters", C.c_void_p)]
+
+
+RASTER_NO_CULL = 1
 
 
 _P = C.c_void_p
@@ -309,8 +313,9 @@ def bin_sort_static(proj: Projected, width, height, bins: Bins, sync=True, strea
 # tgs_rasterize / tgs_rasterize_backward
 
 def rasterize(proj: Projected, bins: Bins, width, height, precision="fp16_tc", bg=(0.0, 0.0, 0.0),
-              out=None, want_n_contrib=True, counters=None, stream=None):
-    """Returns (rgb [3,H,W], T [H,W], n_contrib [H,W] or None)."""
+              out=None, want_n_contrib=True, counters=None, stream=None, cull=True):
+    """Returns (rgb [3,H,W], T [H,W], n_contrib [H,W] or None). cull=False sets
+    TGS_RASTER_NO_CULL (FP16_TC keeps provably-pruned (Gaussian, tile) pairs)."""
     lib = load()
     dev = proj.mean2d.device
     if out is None:
@@ -319,7 +324,8 @@ def rasterize(proj: Projected, bins: Bins, width, height, precision="fp16_tc", b
         nc = torch.empty((height, width), dtype=torch.int32, device=dev) if want_n_contrib else None
     else:
         rgb, T, nc = out
-    o = _RasterOpts(PRECISION[precision], (C.c_float * 3)(*[float(v) for v in bg]), _ptr(counters))
+    o = _RasterOpts(PRECISION[precision], 0 if cull else RASTER_NO_CULL,
+                    (C.c_float * 3)(*[float(v) for v in bg]), _ptr(counters))
     t = _tiling(bins.tiling)
     _check(lib.tgs_rasterize(C.byref(proj.struct()), proj.n, C.byref(bins.struct()), int(width), int(height),
                              C.byref(t), C.byref(o), _ptr(rgb), _ptr(T), _ptr(nc), _stream(stream)))
@@ -334,7 +340,7 @@ def rasterize_backward(proj: Projected, bins: Bins, width, height, T, n_contrib,
     gm = torch.empty((n, 2), dtype=torch.float32, device=dev)
     gco = torch.empty((n, 4), dtype=torch.float32, device=dev)
     gc = torch.empty((n, 3), dtype=torch.float32, device=dev)
-    o = _RasterOpts(PRECISION["fp32"], (C.c_float * 3)(*[float(v) for v in bg]), None)
+    o = _RasterOpts(PRECISION["fp32"], 0, (C.c_float * 3)(*[float(v) for v in bg]), None)
     t = _tiling(bins.tiling)
     g = grad_rgb.contiguous()
     _check(lib.tgs_rasterize_backward(C.byref(proj.struct()), n, C.byref(bins.struct()), int(width),
@@ -383,3 +389,85 @@ class RasterizeFn(torch.autograd.Function):
         proj = Projected(mean2d.shape[0], mean2d, co, rgb, depth, radius, rect)
         gm, gco, gc = rasterize_backward(proj, bins, width, height, T, nc, grad_img, bg)
         return gm, gco, gc, None, None, None, None, None, None, None
+
+
+# ------------------------------------------------------------------------------------------------
+# Graph-captured rendering
+
+class Renderer:
+    """Renders a resident scene from a fixed set of cameras with CUDA graphs.
+
+    Per camera two graphs are captured: one for preprocess + bin sort (asynchronous, no host round
+    trip) and one for rasterize, so a frame is two launches and the GPU never waits on the host
+    between the frame's kernels. Every replay recomputes the frame from the scene in HBM; nothing is
+    cached between frames. Capacities are sized once from a synchronous count per camera
+    (x `margin`); a frame that outgrows its capacity renders background only and reports it through
+    `overflowed()`.
+    """
+
+    def __init__(self, scene: DeviceScene, cameras, tiling=(2, 2), precision="fp16_tc",
+                 bg=(0.0, 0.0, 0.0), margin=1.1, graphs=True, cull=True):
+        self.cull = cull
+        self.scene, self.cameras = scene, list(cameras)
+        self.tiling, self.precision, self.bg = tuple(tiling), precision, tuple(bg)
+        n = scene.n
+        self.proj = Projected.empty(n, scene.means.device)
+        cap = 0
+        for cam in self.cameras:
+            preprocess(scene, cam, out=self.proj)
+            cap = max(cap, bin_sort(self.proj, cam.width, cam.height, self.tiling).entries)
+        W = max(c.width for c in self.cameras)
+        H = max(c.height for c in self.cameras)
+        # bin buffers are shared by all cameras (ranges sized for the largest image)
+        self.bins = allocate_bins(n, int(cap * margin) + 4096, W, H, self.tiling, keys=False)
+        self.out = [(torch.empty((3, c.height, c.width), device=scene.means.device),
+                     torch.empty((c.height, c.width), device=scene.means.device)) for c in self.cameras]
+        self.kernels_per_frame = []
+        self.g_prep, self.g_raster = [], []
+        for k in range(len(self.cameras)):  # run every path once outside capture
+            self._prep(k)
+            self._raster(k)
+        torch.cuda.synchronize()
+        if graphs:
+            side = torch.cuda.Stream()
+            for k in range(len(self.cameras)):
+                before = kernel_launch_count()
+                gp, gr = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+                with torch.cuda.graph(gp, stream=side, capture_error_mode="relaxed"):
+                    self._prep(k)
+                with torch.cuda.graph(gr, stream=side, capture_error_mode="relaxed"):
+                    self._raster(k)
+                self.kernels_per_frame.append(kernel_launch_count() - before)
+                self.g_prep.append(gp)
+                self.g_raster.append(gr)
+            torch.cuda.synchronize()
+
+    def _prep(self, k):
+        cam = self.cameras[k]
+        preprocess(self.scene, cam, out=self.proj)
+        bin_sort(self.proj, cam.width, cam.height, self.tiling, bins=self.bins, sync=False)
+
+    def _raster(self, k):
+        cam = self.cameras[k]
+        rgb, T = self.out[k]
+        rasterize(self.proj, self.bins, cam.width, cam.height, self.precision, self.bg, out=(rgb, T, None),
+                  want_n_contrib=False, cull=self.cull)
+
+    def render(self, k, events=None):
+        """Renders camera k on the current stream; returns (rgb [3,H,W], T [H,W]) (reused buffers).
+        `events`, if given, are three CUDA events recorded before, between and after the two
+        stages."""
+        stream = torch.cuda.current_stream()
+        if events:
+            events[0].record(stream)
+        self.g_prep[k].replay() if self.g_prep else self._prep(k)
+        if events:
+            events[1].record(stream)
+        self.g_raster[k].replay() if self.g_raster else self._raster(k)
+        if events:
+            events[2].record(stream)
+        return self.out[k]
+
+    def overflowed(self) -> bool:
+        """True if the last rendered frame needed more bin entries than the capacity (synchronizes)."""
+        return int(self.bins.num_entries.item()) > self.bins.capacity

@@ -47,6 +47,9 @@ constexpr float kLog2AlphaMax = -0.014499569695115089f;  // log2(0.99)
 // Rows whose FP16 hi/lo error bound 2^-22 * sum_k |q_k| max|f_k| exceeds this (in log2 units)
 // are evaluated by the scalar FP32 path.
 constexpr float kMaxWeightedCoef = 4096.0f;
+// A (Gaussian, tile) pair is skipped when the largest exponent over the tile's pixel box is below
+// log2(1/255) by more than this (log2 units), far above the FP16 exponent error.
+constexpr float kCullMargin = 0.01f;
 constexpr int kLBO = 128;  // bytes between the two K core matrices of an 8-row group
 constexpr int kSBO = 256;  // bytes between 8-row groups
 constexpr int NB = 32;     // list entries per chunk = MMA N
@@ -118,6 +121,26 @@ struct PixState {
   float T, r, g, b, thr;
   int last;
 };
+
+// Smallest value of the quadratic form Q(d) = d^T conic d over the box of offsets
+// d in [dx0, dx1] x [dy0, dy1] (the pixel centres of a tile relative to the Gaussian's mean). Q is
+// convex: its minimum is 0 if the box holds d = 0, else it lies on an edge, where the 1D minimum is
+// at the clamped stationary point. Evaluated through the Cholesky factor, Q = (l11 dx + l12 dy)^2 +
+// (l22 dy)^2, so the result is a sum of squares.
+__device__ __forceinline__ float box_min_quadratic(float a, float b, float c, float3 L, float dx0,
+                                                   float dx1, float dy0, float dy1) {
+  if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return 0.f;
+  auto q = [&](float dx, float dy) {
+    const float u = fmaf(L.x, dx, L.y * dy), v = L.z * dy;
+    return fmaf(u, u, v * v);
+  };
+  const float ia = 1.f / a, ic = 1.f / c;
+  float m = q(dx0, fminf(fmaxf(-b * dx0 * ic, dy0), dy1));
+  m = fminf(m, q(dx1, fminf(fmaxf(-b * dx1 * ic, dy0), dy1)));
+  m = fminf(m, q(fminf(fmaxf(-b * dy0 * ia, dx0), dx1), dy0));
+  m = fminf(m, q(fminf(fmaxf(-b * dy1 * ia, dx0), dx1), dy1));
+  return m;
+}
 
 // Scalar FP32 exponents of a packed entry whose FP16 coefficients would be too inaccurate.
 __device__ __noinline__ float2 scalar_exponents(float px0, float py0, float px1, float py1,
@@ -208,7 +231,7 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD>::kThreads, 1)
                 const float4* __restrict__ conic_opacity, const float* __restrict__ rgb, int width,
                 int height, int GX, float3 bg, float* __restrict__ out_rgb,
                 float* __restrict__ out_T, int* __restrict__ n_contrib,
-                unsigned long long* __restrict__ counters, int32_t* __restrict__ err) {
+                unsigned long long* __restrict__ counters, int32_t* __restrict__ err, int cull) {
   using C = Cfg<GW, GH, NWG, NPROD>;
   constexpr int TILES = C::kTiles;
   constexpr int SLOTS = C::kSlots;
@@ -329,7 +352,13 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD>::kThreads, 1)
 #pragma unroll
       for (int t = 0; t < TILES; ++t) {
         const int tx = gx * GW + (t % GW), ty = gy * GH + (t / GW);
-        const bool active = valid && ((msk >> t) & 1u);
+        bool active = valid && ((msk >> t) & 1u);
+        if (active && cull) {
+          // skip the pair if no pixel of the tile can reach alpha >= 1/255 (exact bound)
+          const float mx = mu.x - (float)(tx * kTile), my = mu.y - (float)(ty * kTile);
+          const float qmin = box_min_quadratic(co.x, co.y, co.z, Lc, -mx, 15.f - mx, -my, 15.f - my);
+          active = fmaf(-0.5f * kLog2e, qmin, lo2) >= kL255 - kCullMargin;
+        }
         const uint32_t bal = __ballot_sync(0xffffffffu, active);
         const uint32_t cnt_t = __popc(bal);
         // active entries are packed to rows 0..cnt-1 in list order; the other lanes fill rows
@@ -614,16 +643,17 @@ tgs_status launch_cfg(const tgs_projected& p, const tgs_bins& b, int width, int 
   auto* cnt = reinterpret_cast<unsigned long long*>(o.counters);
   const float3 bg = make_float3(o.bg[0], o.bg[1], o.bg[2]);
   int32_t* err = device_error_word();
+  const int cull = (o.flags & TGS_RASTER_NO_CULL) ? 0 : 1;
   if (count) {
     auto* k = k_raster_tc<GW, GH, NWG, NPROD, true>;
     TGS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<GX * GY, Cf::kThreads, smem, st>>>(b.ranges, b.vals, b.masks, m2, co, p.rgb, width, height, GX,
-                                           bg, out_rgb, out_T, n_contrib, cnt, err);
+                                           bg, out_rgb, out_T, n_contrib, cnt, err, cull);
   } else {
     auto* k = k_raster_tc<GW, GH, NWG, NPROD, false>;
     TGS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<GX * GY, Cf::kThreads, smem, st>>>(b.ranges, b.vals, b.masks, m2, co, p.rgb, width, height, GX,
-                                           bg, out_rgb, out_T, n_contrib, cnt, err);
+                                           bg, out_rgb, out_T, n_contrib, cnt, err, cull);
   }
   TGS_CHECK_LAUNCH("k_raster_tc");
   return TGS_OK;

@@ -170,22 +170,22 @@ def test_bin_sort_capacity_overflow():
 # ------------------------------------------------------------------------------------------------
 # R4/R5 rasterize
 
-def _raster_vs_oracle(scene, cam, tiling, precision, counters=False):
+def _raster_vs_oracle(scene, cam, tiling, precision, counters=False, cull=True):
     _, proj, bins = _gpu_frame(scene, cam, tiling)
     cnt = torch.zeros(2, dtype=torch.int64, device="cuda") if counters else None
-    rgb, T, nc = tgs.rasterize(proj, bins, cam.width, cam.height, precision, counters=cnt)
+    rgb, T, nc = tgs.rasterize(proj, bins, cam.width, cam.height, precision, counters=cnt, cull=cull)
     torch.cuda.synchronize()
     assert tgs.last_device_error() == 0
     p = _proj_np(proj)
     ob = _oracle_bins(p, cam, tiling)
     img = _oracle_image(p, cam, ob)
-    return (_np(rgb), _np(T), _np(nc), img, (int(_np(cnt)[0]) if counters else None))
+    return (_np(rgb), _np(T), _np(nc), img, (tuple(int(v) for v in _np(cnt)) if counters else None))
 
 
 @pytest.mark.parametrize("tiling", [(1, 1), (2, 2), (4, 2)])
 def test_fp32_raster_parity(case, tiling):
     name, scene, cam = case
-    rgb, T, nc, img, ev = _raster_vs_oracle(scene, cam, tiling, "fp32", counters=True)
+    rgb, T, nc, img, (ev, _) = _raster_vs_oracle(scene, cam, tiling, "fp32", counters=True)
     ok = img.margin > 1e-5
     assert (~ok).mean() < 1e-3
     err = np.abs(rgb - _chw(img.rgb)).max(axis=0)
@@ -199,7 +199,7 @@ def test_fp32_raster_parity(case, tiling):
 @pytest.mark.parametrize("tiling", [(1, 1), (2, 2), (4, 2), (2, 4), (4, 4)])
 def test_tc_raster_parity(case, tiling):
     name, scene, cam = case
-    rgb, T, nc, img, ev = _raster_vs_oracle(scene, cam, tiling, "fp16_tc", counters=True)
+    rgb, T, nc, img, (ev, passing) = _raster_vs_oracle(scene, cam, tiling, "fp16_tc", counters=True)
     ref = _chw(img.rgb)
     psnr = oracle.psnr(rgb, ref)
     assert psnr >= TC_PSNR, psnr
@@ -207,7 +207,33 @@ def test_tc_raster_parity(case, tiling):
     assert (~ok).mean() < 0.02
     err = np.abs(rgb - ref).max(axis=0)
     assert err[ok].max() <= TC_MAXABS, err[ok].max()
-    assert abs(ev - img.evaluated) <= 0.01 * img.evaluated + 10
+    # the tile cull drops pairs that are pruned at every pixel: the passing pairs stay, the
+    # evaluated ones can only shrink
+    assert abs(passing - img.passing) <= 0.01 * img.passing + 10
+    assert ev <= 1.01 * img.evaluated + 10
+
+
+@pytest.mark.parametrize("tiling", [(1, 1), (2, 2), (4, 4)])
+def test_tc_tile_cull_is_exact(case, tiling):
+    # Skipping (Gaussian, tile) pairs whose largest exponent over the tile is below log2(1/255) by
+    # the margin removes only pairs the per-pixel test prunes: the image is bit-identical to the
+    # image without the skip, and the pairs evaluated without it match the oracle's count.
+    name, scene, cam = case
+    _, proj, bins = _gpu_frame(scene, cam, tiling)
+    res = {}
+    for cull in (True, False):
+        cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+        rgb, T, nc = tgs.rasterize(proj, bins, cam.width, cam.height, "fp16_tc", counters=cnt,
+                                   cull=cull)
+        torch.cuda.synchronize()
+        assert tgs.last_device_error() == 0
+        res[cull] = (_np(rgb), _np(T), _np(nc), _np(cnt))
+    for k in range(3):
+        assert np.array_equal(res[True][k], res[False][k]), k
+    assert res[True][3][1] == res[False][3][1]  # passing pairs
+    assert res[True][3][0] <= res[False][3][0]
+    img = _oracle_image(_proj_np(proj), cam, _oracle_bins(_proj_np(proj), cam, tiling))
+    assert abs(int(res[False][3][0]) - img.evaluated) <= 0.01 * img.evaluated + 10
 
 
 def test_grouping_is_exact_on_gpu(case):
