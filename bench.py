@@ -18,9 +18,11 @@ of the scene (independent frames, no collective on the data path): weak scaling.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -198,6 +200,34 @@ def run_reference(args):
     return 0
 
 
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of camera 0 of
+# the 1.5M-Gaussian workload, keyed by the kernel and the SHA-1 of the sources it is built from;
+# reported only while those sources are unchanged (the profile summary gives the command).
+TRAFFIC = {("k_raster_tc", "2x2"): {"bytes": 74296832,
+                                   "sha1": "20c8c29bba74c6741f04ec1957663d1a40ed9f6b"}}
+
+
+def _kernel_sources_sha1(kernel):
+    files = {"k_raster_tc": ["raster_tc.cu", "tgs_internal.cuh"],
+             "k_raster_fp32": ["raster_fp32.cu", "tgs_internal.cuh"]}[kernel]
+    h = hashlib.sha1()
+    for f in files:  # code only: comments and blank lines do not change the kernel
+        with open(os.path.join(ROOT, "paper_2605_17855_gb300", "csrc", f)) as fh:
+            src = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        for line in src.splitlines():
+            line = line.split("//", 1)[0].rstrip()
+            if line:
+                h.update(line.encode() + b"\n")
+    return h.hexdigest()
+
+
+def _traffic(kernel, args):
+    rec = TRAFFIC.get((kernel, args.tiling))
+    if rec is None or rec["sha1"] != _kernel_sources_sha1(kernel):
+        return None
+    return rec["bytes"]
+
+
 def _config(scene, cams, args):
     return {"workload": f"mixture scene, {scene.n} Gaussians (256 clusters, SH degree 3), "
                         f"{len(cams)} orbit cameras at {cams[0].width}x{cams[0].height}",
@@ -258,9 +288,11 @@ def main():
         evs = [[(ev(), ev(), ev()) for _ in cams] for _ in range(steps)]
         t0, t1 = ev(), ev()
         t0.record(stream)
+        torch.cuda.nvtx.range_push(f"timed_{r.precision}_{r.tiling[0]}x{r.tiling[1]}" + ("" if r.cull else "_noskip"))
         for k in range(steps):
             for i in range(len(cams)):
                 r.render(i, evs[k][i])
+        torch.cuda.nvtx.range_pop()
         t1.record(stream)
         torch.cuda.synchronize()
         total_ms = t0.elapsed_time(t1)
@@ -291,6 +323,20 @@ def main():
         ablation = {"value": round(ws * px_per_step / (totnc / steps32 * 1e-3) / 1e6, 3), "unit": UNIT,
                     "rasterize_ms_mean": round(float(rasternc.mean()), 4),
                     "note": "fp16_tc without the exact per-(Gaussian, tile) skip (identical images)"}
+    # the other grouping / precision combinations of the comparison, each timed the same way
+    variants = {}
+    for prec, tl in (("fp32", (2, 2)), ("fp16_tc", (1, 1))):
+        if (prec, tl) == (args.precision, tiling):
+            continue
+        rv = tgs.Renderer(ds, cams, tl, prec)
+        totv, framesv, _, rasterv = timed(rv, steps32, 3)
+        if rv.overflowed():
+            raise RuntimeError("bin capacity overflow during the benchmark")
+        variants[f"{prec}_{tl[0]}x{tl[1]}"] = {
+            "value": round(ws * px_per_step / (totv / steps32 * 1e-3) / 1e6, 3), "unit": UNIT,
+            "rasterize_ms_mean": round(float(rasterv.mean()), 4),
+            "frame_ms_p99": round(float(np.percentile(framesv, 99)), 4)}
+        del rv
     if rend.overflowed() or rend32.overflowed():
         raise RuntimeError("bin capacity overflow during the benchmark")
 
@@ -307,16 +353,23 @@ def main():
               "preprocess_ms_direct": round(e[0].elapsed_time(e[1]), 4),
               "bin_sort_ms_direct": round(e[1].elapsed_time(e[2]), 4)}
 
-    # algorithmic work of the dominant kernel: evaluated pairs and exponentials per launch
+    # algorithmic work of the dominant kernel per launch: the (pixel, entry) pairs evaluated before
+    # termination as the plain algorithm defines them (counted without the tile skip), the pairs
+    # the skip leaves, and the pairs that pass 1/255 (one exponential each)
     cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+    cnt_skip = torch.zeros(2, dtype=torch.int64, device="cuda")
+    entries = 0
     for i, cam in enumerate(cams):
         tgs.preprocess(ds, cam, out=rend.proj)
         tgs.bin_sort(rend.proj, W, H, tiling, bins=rend.bins, sync=False)
-        tgs.rasterize(rend.proj, rend.bins, W, H, args.precision, out=(rend.out[i][0], rend.out[i][1], None),
-                      want_n_contrib=False, counters=cnt)
+        for c, cull in ((cnt, False), (cnt_skip, True)):
+            tgs.rasterize(rend.proj, rend.bins, W, H, args.precision, out=(rend.out[i][0], rend.out[i][1], None),
+                          want_n_contrib=False, counters=c, cull=cull)
+        entries += int(rend.bins.num_entries.item())
     torch.cuda.synchronize()
     pairs, exps = [int(v) / len(cams) for v in cnt.cpu().tolist()]
-    entries = int(rend.bins.num_entries.item())
+    pairs_after_skip = int(cnt_skip[0].item()) / len(cams)
+    entries /= len(cams)
 
     # end to end through the public API: the scene copied host -> device from pinned memory and
     # the 8 images device -> host into pinned memory, every step
@@ -352,18 +405,23 @@ def main():
 
     peaks, peak_kind = _peaks()
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", SM_MAX_MHZ)
-    mufu_peak = SM_COUNT * MUFU_PER_SM_PER_CLK * peaks.get("sm_max_mhz", SM_MAX_MHZ) * 1e6 / 1e9  # Gexp/s
+    mufu_peak = SM_COUNT * MUFU_PER_SM_PER_CLK * peaks.get("sm_max_mhz", SM_MAX_MHZ) * 1e6 / 1e9
     raster_avg_ms = float(raster_ms.mean())
-    achieved = exps / (raster_avg_ms * 1e-3) / 1e9
-    roofline = {"bound": "alu", "kernel": "k_raster_tc" if args.precision == "fp16_tc" else "k_raster_fp32",
-                "achieved": round(achieved, 3), "peak": round(mufu_peak, 1), "unit": "Gexp/s",
-                "frac": round(achieved / mufu_peak, 4), "traffic": None,
-                "peak_source": f"derived: {SM_COUNT} SMs x {MUFU_PER_SM_PER_CLK} MUFU ex2/clk x "
-                               f"{peaks.get('sm_max_mhz', SM_MAX_MHZ):.0f} MHz ({peak_kind} max clock)",
-                "work_per_launch": {"exp_evaluations": exps, "evaluated_pairs": pairs,
-                                    "group_entries": entries},
+    # one evaluated pair costs the plain algorithm one ex2 on the special-function units, the
+    # scarcest unit it uses, so the pair rate is bounded by the MUFU ex2 rate
+    achieved = pairs / (raster_avg_ms * 1e-3) / 1e9
+    kernel = "k_raster_tc" if args.precision == "fp16_tc" else "k_raster_fp32"
+    roofline = {"bound": "alu", "kernel": kernel,
+                "achieved": round(achieved, 2), "peak": round(mufu_peak, 1), "unit": "Gpair/s",
+                "frac": round(achieved / mufu_peak, 4), "traffic": _traffic(kernel, args),
+                "peak_source": f"derived, of measured clock: {SM_COUNT} SMs x {MUFU_PER_SM_PER_CLK} MUFU ex2/clk x "
+                               f"{peaks.get('sm_max_mhz', SM_MAX_MHZ):.0f} MHz ({peak_kind} max SM clock); "
+                               "one ex2 per evaluated (pixel, entry) pair",
+                "work_per_launch": {"evaluated_pairs": pairs, "pairs_after_tile_skip": pairs_after_skip,
+                                    "exp_evaluations": exps, "group_entries": entries},
                 "avg_launch_ms": round(raster_avg_ms, 4),
-                "pair_rate_gps": round(pairs / (raster_avg_ms * 1e-3) / 1e9, 2)}
+                "exp_rate_gexps": round(exps / (raster_avg_ms * 1e-3) / 1e9, 2),
+                "sm_mhz_during_timing": sm_mhz}
 
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
@@ -378,6 +436,7 @@ def main():
                              "preprocess_plus_bin_sort_ms": round(float(prep32.mean()), 4),
                              "rasterize_ms_mean": round(float(raster32.mean()), 4)},
            "fp16_tc_without_tile_skip": ablation,
+           "variants": variants,
            "speedup_vs_fp32_core": round(value / value32, 3),
            "rasterize_speedup_vs_fp32_core": round(float(raster32.mean()) / raster_avg_ms, 3),
            "stages": stages,

@@ -18,6 +18,12 @@
 //     Section 4.2.3 (exact), with the padding slots used for the lo half. |x|, |y| <= 8, so every
 //     feature is an exact FP16 integer. Rows whose FP16 error bound is too large take a scalar
 //     FP32 path in the epilogue instead. The producers are software-pipelined two chunks deep.
+//     Unless disabled, a producer also leaves out of a tile's packed rows every entry whose exact
+//     maximum exponent over the tile's 16x16 pixel centres is below log2(1/255) by a margin (the
+//     minimum of the conic's quadratic form over a box, in closed form): such an entry fails the
+//     pruning test at every pixel of the tile, so the image is unchanged; the tile's MMA rows,
+//     exponent loads and tests for it are saved (a 3-sigma AABB overlaps many tiles the Gaussian
+//     cannot reach at alpha >= 1/255).
 //   * MMA thread: per tile, D[128 px x 32] = A_h[128 x 16] * B_t[32 x 16]^T with
 //     tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 32, K = 16), FP32 accumulators in tensor
 //     memory, double-buffered; completion signalled through tcgen05.commit on mbarriers.
