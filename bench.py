@@ -356,8 +356,8 @@ def main():
     # algorithmic work of the dominant kernel per launch: the (pixel, entry) pairs evaluated before
     # termination as the plain algorithm defines them (counted without the tile skip), the pairs
     # the skip leaves, and the pairs that pass 1/255 (one exponential each)
-    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
-    cnt_skip = torch.zeros(2, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
+    cnt_skip = torch.zeros(3, dtype=torch.int64, device="cuda")
     entries = 0
     for i, cam in enumerate(cams):
         tgs.preprocess(ds, cam, out=rend.proj)
@@ -367,8 +367,9 @@ def main():
                           want_n_contrib=False, counters=c, cull=cull)
         entries += int(rend.bins.num_entries.item())
     torch.cuda.synchronize()
-    pairs, exps = [int(v) / len(cams) for v in cnt.cpu().tolist()]
+    pairs, exps, _ = [int(v) / len(cams) for v in cnt.cpu().tolist()]
     pairs_after_skip = int(cnt_skip[0].item()) / len(cams)
+    slots = int(cnt_skip[2].item()) / len(cams)
     entries /= len(cams)
 
     # end to end through the public API: the scene copied host -> device from pinned memory and
@@ -418,6 +419,7 @@ def main():
                                f"{peaks.get('sm_max_mhz', SM_MAX_MHZ):.0f} MHz ({peak_kind} max SM clock); "
                                "one ex2 per evaluated (pixel, entry) pair",
                 "work_per_launch": {"evaluated_pairs": pairs, "pairs_after_tile_skip": pairs_after_skip,
+                                    "pixel_slots_stepped": slots,
                                     "exp_evaluations": exps, "group_entries": entries},
                 "avg_launch_ms": round(raster_avg_ms, 4),
                 "exp_rate_gexps": round(exps / (raster_avg_ms * 1e-3) / 1e9, 2),

@@ -110,10 +110,12 @@ typedef struct {
   int32_t precision;    /* TGS_PRECISION_* */
   int32_t flags;        /* TGS_RASTER_* */
   float bg[3];          /* background colour added as T_final * bg */
-  int64_t* counters;    /* optional device [2] int64, accumulated: [0] (pixel, entry) pairs
+  int64_t* counters;    /* optional device [3] int64, accumulated: [0] (pixel, entry) pairs
                            evaluated before termination (mask bit set; FP16_TC does not count the
                            pairs of a tile it skipped as provably below 1/255), [1] of those, the
-                           pairs with alpha >= 1/255 (each needs one exp); NULL = not counted */
+                           pairs with alpha >= 1/255 (each needs one exp), [2] (pixel, list slot)
+                           steps the kernel issued, terminated pixels, other tiles' entries and
+                           padding included (its work granularity); NULL = not counted */
 } tgs_raster_opts;
 
 /* ---------------------------------------------------------------------------------------------- */

@@ -324,6 +324,9 @@ def rasterize(proj: Projected, bins: Bins, width, height, precision="fp16_tc", b
         nc = torch.empty((height, width), dtype=torch.int32, device=dev) if want_n_contrib else None
     else:
         rgb, T, nc = out
+    if counters is not None and (counters.dtype != torch.int64 or counters.numel() < 3
+                                 or not counters.is_contiguous() or counters.device != dev):
+        raise ValueError("counters must be a contiguous int64 tensor of 3 elements on the scene's device")
     o = _RasterOpts(PRECISION[precision], 0 if cull else RASTER_NO_CULL,
                     (C.c_float * 3)(*[float(v) for v in bg]), _ptr(counters))
     t = _tiling(bins.tiling)

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(1024) k_raster_fp32(
   }
 
   const uint32_t start = ranges[2 * gid], end = ranges[2 * gid + 1];
-  unsigned long long evaluated = 0, passing = 0;
+  unsigned long long evaluated = 0, passing = 0, slots = 0;
   for (uint32_t base = start; base < end; base += kBatch) {
     bool all_done = true;
 #pragma unroll
@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(1024) k_raster_fp32(
       s_rgb[threadIdx.x] = make_float3(rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2]);
     }
     __syncthreads();
+    if (COUNT) slots += (unsigned long long)cnt * PPT;
     for (int j = 0; j < cnt; ++j) {
       const uint32_t m = s_mask[j];
       const float2 xy = s_xy[j];
@@ -112,10 +113,12 @@ __global__ void __launch_bounds__(1024) k_raster_fp32(
     for (int o = 16; o > 0; o >>= 1) {
       evaluated += __shfl_xor_sync(0xffffffffu, evaluated, o);
       passing += __shfl_xor_sync(0xffffffffu, passing, o);
+      slots += __shfl_xor_sync(0xffffffffu, slots, o);
     }
     if ((threadIdx.x & 31) == 0) {
       if (evaluated) atomicAdd(counters, evaluated);
       if (passing) atomicAdd(counters + 1, passing);
+      if (slots) atomicAdd(counters + 2, slots);
     }
   }
 }

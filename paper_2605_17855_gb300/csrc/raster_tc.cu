@@ -157,10 +157,10 @@ __device__ __noinline__ float2 scalar_exponents(float px0, float py0, float px1,
   return make_float2(e0, e1);
 }
 
-// One front-to-back step (Section 2) for one pixel, predicated. The caller has voted that some lane
-// of the warp may pass; the pruning test is repeated here against the pixel's live threshold.
-// D = log2(o e^power) already contains the opacity, so alpha = min(0.99, 2^D) = 2^min(D, log2 0.99).
-template <bool COUNT>
+// One front-to-back step (Section 2) for one pixel, branch-free: the pruning test against the
+// pixel's live threshold predicates the update. D = log2(o e^power) already contains the opacity,
+// so alpha = min(0.99, 2^D) = 2^min(D, log2 0.99). NC: track the last blended list position.
+template <bool COUNT, bool NC>
 __device__ __forceinline__ void blend_step(float e, const float4& rc, PixState& s, int pos,
                                            unsigned long long& passing) {
   const bool p = e >= s.thr;                 // alpha >= 1/255 and the pixel is live
@@ -174,21 +174,36 @@ __device__ __forceinline__ void blend_step(float e, const float4& rc, PixState& 
     s.g = fmaf(w, rc.y, s.g);
     s.b = fmaf(w, rc.z, s.b);
     s.T = Tn;
-    s.last = pos;
+    if (NC) s.last = pos;
   }
   if (term) s.thr = inf_f();
 }
 
+// One packed entry (column jj of granule g) blended into the thread's two pixels.
+template <int TILES, bool COUNT, bool NC>
+__device__ __forceinline__ void blend_column(float e0, float e1, int j, int base,
+                                             const Slot<TILES>& sl, int t, PixState& s0,
+                                             PixState& s1, unsigned long long& evaluated,
+                                             unsigned long long& passing) {
+  if (COUNT) evaluated += (s0.thr < inf_f()) + (s1.thr < inf_f());
+  const float4 rc = sl.rgbc[t][j];
+  const int pos = NC ? base + (int)sl.entry[t][j] + 1 : 0;
+  blend_step<COUNT, NC>(e0, rc, s0, pos, passing);
+  blend_step<COUNT, NC>(e1, rc, s1, pos, passing);
+}
+
 // Blends one 8-column granule (packed entries 8g .. 8g+7 of tile t) into the thread's two pixels.
-// d[0..7] are pixel 0's exponents, d[8..15] pixel 1's. All sixteen prune tests and warp votes are
-// issued before any blend so that they pipeline; padded columns (>= cnt) hold a never-passing
-// exponent.
-template <int TILES, bool COUNT>
+// d[0..7] are pixel 0's exponents, d[8..15] pixel 1's. The steps are predicated, not branched per
+// column, so the exponentials and tests of different columns and pixels overlap; a granule that
+// is cut by the end of the tile's packed entries only runs its valid columns.
+template <int TILES, bool COUNT, bool NC>
 __device__ __forceinline__ void blend_granule(const uint32_t (&d)[16], int g, int cnt, uint32_t sb,
                                               int base, const Slot<TILES>& sl, int t, int tx,
                                               int ty, int quarter, int lane, PixState& s0,
                                               PixState& s1, unsigned long long& evaluated,
-                                              unsigned long long& passing) {
+                                              unsigned long long& passing,
+                                              unsigned long long& slots) {
+  if (COUNT) slots += 16;
   float e0[8], e1[8];
 #pragma unroll
   for (int jj = 0; jj < 8; ++jj) {
@@ -211,26 +226,22 @@ __device__ __forceinline__ void blend_granule(const uint32_t (&d)[16], int g, in
         e1[jj] = es.y;
       }
   }
-  bool v0[8], v1[8];
+  const int ncols = cnt - 8 * g;  // >= 1; warp-uniform
+  if (ncols >= 8) {
 #pragma unroll
-  for (int jj = 0; jj < 8; ++jj) {
-    v0[jj] = __any_sync(0xffffffffu, e0[jj] >= s0.thr);
-    v1[jj] = __any_sync(0xffffffffu, e1[jj] >= s1.thr);
-  }
+    for (int jj = 0; jj < 8; ++jj)
+      blend_column<TILES, COUNT, NC>(e0[jj], e1[jj], 8 * g + jj, base, sl, t, s0, s1, evaluated,
+                                     passing);
+  } else {
 #pragma unroll
-  for (int jj = 0; jj < 8; ++jj) {
-    if (COUNT && 8 * g + jj < cnt) evaluated += (s0.thr < inf_f()) + (s1.thr < inf_f());
-    if (v0[jj] || v1[jj]) {
-      const int j = 8 * g + jj;
-      const float4 rc = sl.rgbc[t][j];
-      const int pos = base + (int)sl.entry[t][j] + 1;
-      if (v0[jj]) blend_step<COUNT>(e0[jj], rc, s0, pos, passing);
-      if (v1[jj]) blend_step<COUNT>(e1[jj], rc, s1, pos, passing);
-    }
+    for (int jj = 0; jj < 7; ++jj)
+      if (jj < ncols)
+        blend_column<TILES, COUNT, NC>(e0[jj], e1[jj], 8 * g + jj, base, sl, t, s0, s1, evaluated,
+                                       passing);
   }
 }
 
-template <int GW, int GH, int NWG, int NPROD, bool COUNT>
+template <int GW, int GH, int NWG, int NPROD, bool COUNT, bool NC>
 __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD>::kThreads, 1)
     k_raster_tc(const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ vals,
                 const uint16_t* __restrict__ masks, const float2* __restrict__ mean2d,
@@ -501,7 +512,7 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD>::kThreads, 1)
       wdone[r] = __all_sync(0xffffffffu, all);
     }
     bool counted_done = false;
-    unsigned long long evaluated = 0, passing = 0;
+    unsigned long long evaluated = 0, passing = 0, slots = 0;
     int job = 0;
     bool finished = false;
     for (int c = 0; !finished; ++c) {
@@ -548,8 +559,8 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD>::kThreads, 1)
               __syncwarp();
               if (lane == 0) mbar_arrive(&S.tempty[st]);
             }
-            blend_granule<TILES, COUNT>(ga, g, cnt, sb, base, sl, t, tx, ty, quarter, lane,
-                                        ps[r][0], ps[r][1], evaluated, passing);
+            blend_granule<TILES, COUNT, NC>(ga, g, cnt, sb, base, sl, t, tx, ty, quarter, lane,
+                                        ps[r][0], ps[r][1], evaluated, passing, slots);
             if (g + 1 < ngr) {
               tmem_wait_ld(gb);
               if (g + 2 < ngr) {
@@ -560,8 +571,8 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD>::kThreads, 1)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&S.tempty[st]);
               }
-              blend_granule<TILES, COUNT>(gb, g + 1, cnt, sb, base, sl, t, tx, ty, quarter, lane,
-                                          ps[r][0], ps[r][1], evaluated, passing);
+              blend_granule<TILES, COUNT, NC>(gb, g + 1, cnt, sb, base, sl, t, tx, ty, quarter, lane,
+                                          ps[r][0], ps[r][1], evaluated, passing, slots);
               if (g + 2 < ngr) tmem_wait_ld(ga);
             }
           }
@@ -611,10 +622,12 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD>::kThreads, 1)
       for (int o = 16; o > 0; o >>= 1) {
         evaluated += __shfl_xor_sync(0xffffffffu, evaluated, o);
         passing += __shfl_xor_sync(0xffffffffu, passing, o);
+        slots += __shfl_xor_sync(0xffffffffu, slots, o);
       }
       if (lane == 0) {
         if (evaluated) atomicAdd(counters, evaluated);
         if (passing) atomicAdd(counters + 1, passing);
+        if (slots) atomicAdd(counters + 2, slots);
       }
     }
   }
@@ -650,17 +663,20 @@ tgs_status launch_cfg(const tgs_projected& p, const tgs_bins& b, int width, int 
   const float3 bg = make_float3(o.bg[0], o.bg[1], o.bg[2]);
   int32_t* err = device_error_word();
   const int cull = (o.flags & TGS_RASTER_NO_CULL) ? 0 : 1;
-  if (count) {
-    auto* k = k_raster_tc<GW, GH, NWG, NPROD, true>;
+  auto launch = [&](auto* k) -> tgs_status {
     TGS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k<<<GX * GY, Cf::kThreads, smem, st>>>(b.ranges, b.vals, b.masks, m2, co, p.rgb, width, height, GX,
-                                           bg, out_rgb, out_T, n_contrib, cnt, err, cull);
-  } else {
-    auto* k = k_raster_tc<GW, GH, NWG, NPROD, false>;
-    TGS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k<<<GX * GY, Cf::kThreads, smem, st>>>(b.ranges, b.vals, b.masks, m2, co, p.rgb, width, height, GX,
-                                           bg, out_rgb, out_T, n_contrib, cnt, err, cull);
-  }
+    k<<<GX * GY, Cf::kThreads, smem, st>>>(b.ranges, b.vals, b.masks, m2, co, p.rgb, width, height,
+                                           GX, bg, out_rgb, out_T, n_contrib, cnt, err, cull);
+    return TGS_OK;
+  };
+  tgs_status s;
+  if (count)
+    s = n_contrib ? launch(k_raster_tc<GW, GH, NWG, NPROD, true, true>)
+                  : launch(k_raster_tc<GW, GH, NWG, NPROD, true, false>);
+  else
+    s = n_contrib ? launch(k_raster_tc<GW, GH, NWG, NPROD, false, true>)
+                  : launch(k_raster_tc<GW, GH, NWG, NPROD, false, false>);
+  if (s != TGS_OK) return s;
   TGS_CHECK_LAUNCH("k_raster_tc");
   return TGS_OK;
 }

@@ -172,7 +172,7 @@ def test_bin_sort_capacity_overflow():
 
 def _raster_vs_oracle(scene, cam, tiling, precision, counters=False, cull=True):
     _, proj, bins = _gpu_frame(scene, cam, tiling)
-    cnt = torch.zeros(2, dtype=torch.int64, device="cuda") if counters else None
+    cnt = torch.zeros(3, dtype=torch.int64, device="cuda") if counters else None
     rgb, T, nc = tgs.rasterize(proj, bins, cam.width, cam.height, precision, counters=cnt, cull=cull)
     torch.cuda.synchronize()
     assert tgs.last_device_error() == 0
@@ -185,7 +185,7 @@ def _raster_vs_oracle(scene, cam, tiling, precision, counters=False, cull=True):
 @pytest.mark.parametrize("tiling", [(1, 1), (2, 2), (4, 2)])
 def test_fp32_raster_parity(case, tiling):
     name, scene, cam = case
-    rgb, T, nc, img, (ev, _) = _raster_vs_oracle(scene, cam, tiling, "fp32", counters=True)
+    rgb, T, nc, img, (ev, _, _) = _raster_vs_oracle(scene, cam, tiling, "fp32", counters=True)
     ok = img.margin > 1e-5
     assert (~ok).mean() < 1e-3
     err = np.abs(rgb - _chw(img.rgb)).max(axis=0)
@@ -199,7 +199,7 @@ def test_fp32_raster_parity(case, tiling):
 @pytest.mark.parametrize("tiling", [(1, 1), (2, 2), (4, 2), (2, 4), (4, 4)])
 def test_tc_raster_parity(case, tiling):
     name, scene, cam = case
-    rgb, T, nc, img, (ev, passing) = _raster_vs_oracle(scene, cam, tiling, "fp16_tc", counters=True)
+    rgb, T, nc, img, (ev, passing, _) = _raster_vs_oracle(scene, cam, tiling, "fp16_tc", counters=True)
     ref = _chw(img.rgb)
     psnr = oracle.psnr(rgb, ref)
     assert psnr >= TC_PSNR, psnr
@@ -222,7 +222,7 @@ def test_tc_tile_cull_is_exact(case, tiling):
     _, proj, bins = _gpu_frame(scene, cam, tiling)
     res = {}
     for cull in (True, False):
-        cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+        cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
         rgb, T, nc = tgs.rasterize(proj, bins, cam.width, cam.height, "fp16_tc", counters=cnt,
                                    cull=cull)
         torch.cuda.synchronize()
