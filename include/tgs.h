@@ -93,7 +93,7 @@ typedef struct {
 
 /* Sorted group-level entries (Section 4.4.2). Arrays are caller-allocated device memory. */
 typedef struct {
-  int64_t capacity;     /* number of entries keys/vals/masks can hold (< 2^32) */
+  int64_t capacity;     /* number of entries keys/vals/masks can hold (< 2^30) */
   uint64_t* keys;       /* [capacity] (group id << 32) | bits(float depth), ascending; may be NULL */
   uint32_t* vals;       /* [capacity] Gaussian index of each entry */
   uint16_t* masks;      /* [capacity] tile-membership bits, bit (ty%gh)*gw + (tx%gw) */
@@ -138,7 +138,8 @@ tgs_status tgs_check_device(int32_t device);
 tgs_status tgs_preprocess(const tgs_scene* scene, const tgs_camera* cam, tgs_projected* out,
                           void* stream);
 
-/* Workspace bytes tgs_bin_sort needs for n Gaussians, `capacity` entries and the image/tiling. */
+/* Workspace bytes tgs_bin_sort needs for n Gaussians, `capacity` entries and the image/tiling
+ * (n < 2^30 and capacity < 2^30, else TGS_ERR_INVALID_ARGUMENT). */
 tgs_status tgs_bin_sort_workspace_size(int64_t n, int64_t capacity, int32_t width, int32_t height,
                                        const tgs_tiling* tiling, size_t* bytes);
 

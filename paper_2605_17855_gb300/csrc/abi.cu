@@ -50,10 +50,8 @@ static bool valid_tiling(const tgs_tiling* t) {
 
 static bool valid_size(int32_t w, int32_t h) { return w >= 1 && h >= 1 && w <= 16384 && h <= 16384; }
 
-static int num_groups(int32_t w, int32_t h, const tgs_tiling* t) {
-  const int tx = div_up(w, kTile), ty = div_up(h, kTile);
-  return div_up(tx, t->group_w) * div_up(ty, t->group_h);
-}
+static int group_cols(int32_t w, const tgs_tiling* t) { return div_up(div_up(w, kTile), t->group_w); }
+static int group_rows(int32_t h, const tgs_tiling* t) { return div_up(div_up(h, kTile), t->group_h); }
 
 static tgs_status require_sm103(int32_t device) {
   cudaDeviceProp prop;
@@ -127,9 +125,9 @@ tgs_status tgs_bin_sort_workspace_size(int64_t n, int64_t capacity, int32_t widt
                                        const tgs_tiling* tiling, size_t* bytes) {
   g_msg[0] = 0;
   if (!bytes || !valid_tiling(tiling) || !valid_size(width, height) || n < 0 || capacity < 0 ||
-      capacity >= (int64_t(1) << 32) || n >= (int64_t(1) << 31))
+      capacity >= (int64_t(1) << 30) || n >= (int64_t(1) << 30))
     return set_error("bad argument"), TGS_ERR_INVALID_ARGUMENT;
-  *bytes = bin_sort_workspace_bytes(n, capacity, num_groups(width, height, tiling));
+  *bytes = bin_sort_workspace_bytes(n, capacity, group_cols(width, tiling), group_rows(height, tiling));
   return TGS_OK;
 }
 
@@ -138,15 +136,16 @@ tgs_status tgs_bin_sort(const tgs_projected* proj, int64_t n, int32_t width, int
                         tgs_bins* bins, int64_t* num_entries_host, void* stream) {
   g_msg[0] = 0;
   if (!proj || !bins || !valid_tiling(tiling) || !valid_size(width, height) || n < 0 ||
-      n >= (int64_t(1) << 31))
+      n >= (int64_t(1) << 30))
     return set_error("bad argument"), TGS_ERR_INVALID_ARGUMENT;
-  if (bins->capacity < 0 || bins->capacity >= (int64_t(1) << 32))
+  if (bins->capacity < 0 || bins->capacity >= (int64_t(1) << 30))
     return set_error("capacity out of range"), TGS_ERR_INVALID_ARGUMENT;
   if (!bins->ranges || !bins->num_entries || (bins->capacity > 0 && (!bins->vals || !bins->masks)))
     return set_error("null bins array"), TGS_ERR_INVALID_ARGUMENT;
   if (n > 0 && (!proj->rect || !proj->depth || !proj->radius))
     return set_error("null projected array"), TGS_ERR_INVALID_ARGUMENT;
-  const size_t need = bin_sort_workspace_bytes(n, bins->capacity, num_groups(width, height, tiling));
+  const size_t need = bin_sort_workspace_bytes(n, bins->capacity, group_cols(width, tiling),
+                                               group_rows(height, tiling));
   if (workspace_bytes < need || (need > 0 && !workspace) || ((uintptr_t)workspace & 255))
     return set_error("workspace too small or misaligned: need %zu bytes", need),
            TGS_ERR_INVALID_ARGUMENT;

@@ -39,7 +39,7 @@ inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 // Launchers implemented by the kernel translation units.
 tgs_status launch_preprocess(const tgs_scene& s, const tgs_camera& cam, const tgs_projected& out,
                              cudaStream_t st);
-size_t bin_sort_workspace_bytes(int64_t n, int64_t capacity, int num_groups);
+size_t bin_sort_workspace_bytes(int64_t n, int64_t capacity, int GX, int GY);
 tgs_status launch_bin_sort(const tgs_projected& p, int64_t n, int width, int height, int gw, int gh,
                            void* ws, size_t ws_bytes, const tgs_bins& bins, cudaStream_t st);
 tgs_status launch_raster_fp32(const tgs_projected& p, const tgs_bins& b, int width, int height,
