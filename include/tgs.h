@@ -211,6 +211,95 @@ int64_t tgs_kernel_launch_count(void);
  * a kernel whose bounded wait expired. Synchronizes the device. reset != 0 clears it. */
 tgs_status tgs_last_device_error(int32_t reset);
 
+/* ---------------------------------------------------------------------------------------------
+ * Rendering service (tgs_serve_*): resident scenes and asynchronous frame requests.
+ *
+ * A server owns device copies of its scenes and a worker thread that renders requests with the
+ * calls above (preprocess, bin sort, rasterize). It keeps `slots` frames in flight, each on its own
+ * CUDA stream with its own buffers; a request enters a slot as soon as one frees (continuous
+ * batching: requests of different scenes and resolutions overlap on the GPU), in submission
+ * order. All device memory of the server (scenes and slot buffers) counts against
+ * hbm_budget_bytes. A slot's bin capacity starts at 4 entries per Gaussian and grows when a frame
+ * needs more (the frame is then rendered again; counted in `regrown`).
+ *
+ * Requests are identified by tickets. A ticket's record is released when poll or wait reports it
+ * done; later calls with it return TGS_ERR_NOT_FOUND. Waits are bounded: tgs_serve_wait returns
+ * TGS_ERR_TIMEOUT after timeout_ms, and a request not finished within request_timeout_ms (if > 0)
+ * completes with TGS_ERR_TIMEOUT (its slot is reused once the GPU has finished its work).
+ * Functions may be called from any host thread; a server must not be used after destroy. */
+
+typedef struct {
+  int64_t hbm_budget_bytes;   /* device bytes the server may hold (scenes + slot buffers) */
+  int32_t max_inflight;       /* queued + rendering requests admitted at once (>= 1) */
+  int32_t slots;              /* frames rendered concurrently (1..16) */
+  int32_t device;             /* CUDA device ordinal (must be sm_103) */
+  int32_t precision;          /* TGS_PRECISION_* */
+  tgs_tiling tiling;          /* tile grouping of every frame */
+  float bg[3];                /* background colour */
+  int32_t request_timeout_ms; /* 0 = no limit */
+} tgs_serve_config;
+
+typedef struct tgs_server tgs_server; /* opaque */
+
+#define TGS_SERVE_MAX_RESOLUTIONS 16
+typedef struct {
+  int32_t width, height;
+  int64_t completed;          /* requests of this resolution completed with TGS_OK */
+  double mean_ms, p50_ms, p99_ms; /* submit -> completion latency over the last 4096 of them */
+} tgs_serve_resolution_stats;
+
+typedef struct {
+  int64_t submitted;          /* admitted requests */
+  int64_t rejected;           /* submissions refused with TGS_ERR_BUSY */
+  int64_t completed;          /* requests completed with TGS_OK */
+  int64_t failed;             /* requests completed with an error (including time-outs) */
+  int64_t regrown;            /* frames rendered again after a bin capacity increase */
+  int64_t inflight;           /* queued + rendering now */
+  int64_t hbm_bytes;          /* device bytes held by the server now */
+  double seconds;             /* since tgs_serve_create */
+  double frames_per_second;   /* completed / seconds */
+  int32_t num_resolutions;
+  tgs_serve_resolution_stats res[TGS_SERVE_MAX_RESOLUTIONS]; /* in order of first appearance */
+} tgs_serve_stats;
+
+/* Creates a server and its worker thread on config->device. INVALID_ARGUMENT for a bad config,
+ * UNSUPPORTED_DEVICE if the device is not sm_103, CUDA if a stream cannot be created. */
+tgs_status tgs_serve_create(const tgs_serve_config* config, tgs_server** out);
+
+/* Copies a scene (the arrays of `scene` may be host or device memory) into server-owned device
+ * memory and returns its id. CAPACITY if the copy would exceed the budget. Synchronous. */
+tgs_status tgs_serve_add_scene(tgs_server* server, const tgs_scene* scene, int32_t* scene_id);
+
+/* Frees a scene. BUSY while admitted requests use it, NOT_FOUND for an unknown id. */
+tgs_status tgs_serve_remove_scene(tgs_server* server, int32_t scene_id);
+
+/* Admits a request to render `scene_id` from `camera` into out_rgb (device [3,H,W] planar) and,
+ * if non-NULL, out_T (device [H,W]); both are caller-owned and must stay valid until the request
+ * is done. Returns at once with a ticket. BUSY if max_inflight requests are admitted already;
+ * NOT_FOUND for an unknown scene; INVALID_ARGUMENT for a bad camera or NULL out_rgb. A request
+ * whose buffers cannot fit the budget completes with CAPACITY. */
+tgs_status tgs_serve_submit(tgs_server* server, int32_t scene_id, const tgs_camera* camera,
+                            float* out_rgb, float* out_T, uint64_t* ticket);
+
+/* Non-blocking: *done = 1 and *result = the request's status if it has completed (the ticket is
+ * then released), else *done = 0. NOT_FOUND for an unknown ticket. */
+tgs_status tgs_serve_poll(tgs_server* server, uint64_t ticket, int32_t* done, tgs_status* result);
+
+/* Blocks until the request completes (then as poll) or timeout_ms passes (TGS_ERR_TIMEOUT, the
+ * ticket stays valid). */
+tgs_status tgs_serve_wait(tgs_server* server, uint64_t ticket, int32_t timeout_ms,
+                          tgs_status* result);
+
+/* Pause (paused != 0) or resume moving queued requests into slots. Frames already in slots
+ * finish; submissions are still admitted up to max_inflight. */
+tgs_status tgs_serve_pause(tgs_server* server, int32_t paused);
+
+tgs_status tgs_serve_get_stats(tgs_server* server, tgs_serve_stats* out);
+
+/* Stops the worker, waits (bounded) for the frames in slots, frees all device memory and the
+ * server. Requests still queued are dropped. */
+tgs_status tgs_serve_destroy(tgs_server* server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,13 @@ TILE = 16
 PRECISION = {"fp32": 0, "fp16_tc": 1}
 
 TGS_OK = 0
+TGS_ERR_INVALID_ARGUMENT = 1
+TGS_ERR_CUDA = 2
 TGS_ERR_CAPACITY = 3
+TGS_ERR_UNSUPPORTED_DEVICE = 4
+TGS_ERR_TIMEOUT = 5
+TGS_ERR_BUSY = 6
+TGS_ERR_NOT_FOUND = 7
 
 
 class TgsError(RuntimeError):
@@ -77,6 +83,28 @@ _lib = None
 _lock = threading.Lock()
 
 # name -> (restype, argtypes) of every exported function
+class _ServeConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_inflight", C.c_int32), ("slots", C.c_int32),
+                ("device", C.c_int32), ("precision", C.c_int32), ("tiling", _Tiling),
+                ("bg", C.c_float * 3), ("request_timeout_ms", C.c_int32)]
+
+
+SERVE_MAX_RESOLUTIONS = 16
+
+
+class _ServeResolutionStats(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("completed", C.c_int64),
+                ("mean_ms", C.c_double), ("p50_ms", C.c_double), ("p99_ms", C.c_double)]
+
+
+class _ServeStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("rejected", C.c_int64), ("completed", C.c_int64),
+                ("failed", C.c_int64), ("regrown", C.c_int64), ("inflight", C.c_int64),
+                ("hbm_bytes", C.c_int64), ("seconds", C.c_double), ("frames_per_second", C.c_double),
+                ("num_resolutions", C.c_int32),
+                ("res", _ServeResolutionStats * SERVE_MAX_RESOLUTIONS)]
+
+
 SIGNATURES = {
     "tgs_status_string": (C.c_char_p, [C.c_int32]),
     "tgs_last_error_message": (C.c_char_p, []),
@@ -96,6 +124,15 @@ SIGNATURES = {
                                            _P, _P, _P, _P, _P]),
     "tgs_last_device_error": (C.c_int32, [C.c_int32]),
     "tgs_kernel_launch_count": (C.c_int64, []),
+    "tgs_serve_create": (C.c_int32, [C.POINTER(_ServeConfig), C.POINTER(_P)]),
+    "tgs_serve_add_scene": (C.c_int32, [_P, C.POINTER(_Scene), C.POINTER(C.c_int32)]),
+    "tgs_serve_remove_scene": (C.c_int32, [_P, C.c_int32]),
+    "tgs_serve_submit": (C.c_int32, [_P, C.c_int32, C.POINTER(_Camera), _P, _P, C.POINTER(C.c_uint64)]),
+    "tgs_serve_poll": (C.c_int32, [_P, C.c_uint64, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "tgs_serve_wait": (C.c_int32, [_P, C.c_uint64, C.c_int32, C.POINTER(C.c_int32)]),
+    "tgs_serve_pause": (C.c_int32, [_P, C.c_int32]),
+    "tgs_serve_get_stats": (C.c_int32, [_P, C.POINTER(_ServeStats)]),
+    "tgs_serve_destroy": (C.c_int32, [_P]),
 }
 
 
@@ -474,3 +511,103 @@ class Renderer:
     def overflowed(self) -> bool:
         """True if the last rendered frame needed more bin entries than the capacity (synchronizes)."""
         return int(self.bins.num_entries.item()) > self.bins.capacity
+
+
+# ------------------------------------------------------------------------------------------------
+# Rendering service
+
+class Server:
+    """A tgs_server: resident scenes and asynchronous frame requests rendered by a native worker
+    thread with `slots` frames in flight (see include/tgs.h, tgs_serve_*). Use as a context manager
+    or call close()."""
+
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 64, slots: int = 4, device: int = 0,
+                 precision: str = "fp16_tc", tiling=(2, 2), bg=(0.0, 0.0, 0.0), request_timeout_ms: int = 0):
+        lib = load()
+        cfg = _ServeConfig(int(hbm_budget_bytes), int(max_inflight), int(slots), int(device),
+                           PRECISION[precision], _tiling(tiling), (C.c_float * 3)(*[float(v) for v in bg]),
+                           int(request_timeout_ms))
+        h = _P()
+        _check(lib.tgs_serve_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+        self.device = device
+
+    def _handle(self):
+        if self._h is None:
+            raise ValueError("server is closed")
+        return self._h
+
+    def add_scene(self, scene) -> int:
+        """Copies a DeviceScene (or any object with the same array fields on the host as numpy)
+        into the server; returns its id."""
+        if isinstance(scene, DeviceScene):
+            st = scene.struct()
+            keep = scene
+        else:  # host arrays: the library copies them with cudaMemcpyDefault
+            arrs = [np.ascontiguousarray(getattr(scene, k), np.float32)
+                    for k in ("means", "scales", "quats", "opacities", "sh")]
+            keep = arrs
+            st = _Scene(int(arrs[0].shape[0]), int(scene.sh_degree),
+                        *[a.ctypes.data if a.size else None for a in arrs])
+        sid = C.c_int32()
+        _check(load().tgs_serve_add_scene(self._handle(), C.byref(st), C.byref(sid)))
+        del keep
+        return int(sid.value)
+
+    def remove_scene(self, scene_id: int):
+        _check(load().tgs_serve_remove_scene(self._handle(), int(scene_id)))
+
+    def submit(self, scene_id: int, cam, out_rgb, out_T=None) -> int:
+        """Admits a request; returns its ticket. out_rgb [3,H,W] (and out_T [H,W]) are device
+        tensors that must stay alive until the request is done. Raises TgsError (BUSY when full)."""
+        t = C.c_uint64()
+        c = camera_struct(cam)
+        _check(load().tgs_serve_submit(self._handle(), int(scene_id), C.byref(c), _ptr(out_rgb),
+                                       _ptr(out_T), C.byref(t)))
+        return int(t.value)
+
+    def try_submit(self, scene_id: int, cam, out_rgb, out_T=None):
+        """As submit, but returns None instead of raising when the server is full."""
+        t = C.c_uint64()
+        c = camera_struct(cam)
+        st = load().tgs_serve_submit(self._handle(), int(scene_id), C.byref(c), _ptr(out_rgb),
+                                     _ptr(out_T), C.byref(t))
+        if st == TGS_ERR_BUSY:
+            return None
+        _check(st)
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        """None while running, else the request's status (the ticket is then released)."""
+        done, res = C.c_int32(), C.c_int32()
+        _check(load().tgs_serve_poll(self._handle(), C.c_uint64(ticket), C.byref(done), C.byref(res)))
+        return int(res.value) if done.value else None
+
+    def wait(self, ticket: int, timeout_ms: int = 10000) -> int:
+        """The request's status; raises TgsError(TIMEOUT) if it is not done in time."""
+        res = C.c_int32()
+        _check(load().tgs_serve_wait(self._handle(), C.c_uint64(ticket), int(timeout_ms), C.byref(res)))
+        return int(res.value)
+
+    def pause(self, paused: bool = True):
+        _check(load().tgs_serve_pause(self._handle(), 1 if paused else 0))
+
+    def stats(self) -> dict:
+        st = _ServeStats()
+        _check(load().tgs_serve_get_stats(self._handle(), C.byref(st)))
+        out = {k: getattr(st, k) for k, _ in _ServeStats._fields_ if k not in ("res", "num_resolutions")}
+        out["resolutions"] = [{k: getattr(st.res[i], k) for k, _ in _ServeResolutionStats._fields_}
+                              for i in range(st.num_resolutions)]
+        return out
+
+    def close(self):
+        if self._h is not None:
+            h, self._h = self._h, None
+            _check(load().tgs_serve_destroy(h))
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+

@@ -30,7 +30,9 @@ def lib():
 
 def test_header_declares_the_boundary():
     names = _declared_functions()
-    for required in ("tgs_preprocess", "tgs_bin_sort", "tgs_rasterize", "tgs_rasterize_backward"):
+    for required in ("tgs_preprocess", "tgs_bin_sort", "tgs_rasterize", "tgs_rasterize_backward",
+                     "tgs_serve_create", "tgs_serve_add_scene", "tgs_serve_submit", "tgs_serve_poll",
+                     "tgs_serve_wait", "tgs_serve_get_stats", "tgs_serve_destroy"):
         assert required in names
 
 
@@ -107,3 +109,21 @@ def test_oracle_never_imports_the_product():
         assert "paper_2605_17855_gb300" not in _imports(p), p
     for p in glob.glob(os.path.join(ROOT, "oracle", "*.[ch]")):
         assert "tgs_internal" not in open(p).read() and "tgs.h" not in open(p).read()
+
+
+def test_serve_argument_validation_is_host_side(lib):
+    import ctypes as C
+
+    import paper_2605_17855_gb300 as tgs
+    h = C.c_void_p()
+    bad = tgs._ServeConfig(0, 4, 2, 0, 1, tgs._Tiling(2, 2), (C.c_float * 3)(0, 0, 0), 0)  # no budget
+    assert lib.tgs_serve_create(C.byref(bad), C.byref(h)) == tgs.TGS_ERR_INVALID_ARGUMENT
+    bad = tgs._ServeConfig(1 << 30, 0, 2, 0, 1, tgs._Tiling(2, 2), (C.c_float * 3)(0, 0, 0), 0)
+    assert lib.tgs_serve_create(C.byref(bad), C.byref(h)) == tgs.TGS_ERR_INVALID_ARGUMENT
+    bad = tgs._ServeConfig(1 << 30, 4, 17, 0, 1, tgs._Tiling(2, 2), (C.c_float * 3)(0, 0, 0), 0)
+    assert lib.tgs_serve_create(C.byref(bad), C.byref(h)) == tgs.TGS_ERR_INVALID_ARGUMENT
+    assert lib.tgs_serve_create(None, C.byref(h)) == tgs.TGS_ERR_INVALID_ARGUMENT
+    st = tgs._ServeStats()
+    assert lib.tgs_serve_get_stats(None, C.byref(st)) == tgs.TGS_ERR_INVALID_ARGUMENT
+    assert lib.tgs_serve_destroy(None) == tgs.TGS_ERR_INVALID_ARGUMENT
+
