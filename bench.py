@@ -35,6 +35,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "rasterize Mpx/s & p99 frame ms, FP16-TC vs FP32-core, PSNR>=45dB vs oracle"
+DTYPE = {"fp16_tc": "f16 products, f32 accumulate/blend", "bf16_tc": "bf16 products, f32 accumulate/blend",
+         "fp32": "f32"}
 UNIT = "Mpx/s"
 MUFU_PER_SM_PER_CLK = 16  # ex2 results per SM per clock (special-function units)
 SM_COUNT = 152
@@ -238,7 +240,7 @@ def run_serve(args):
     done = st["completed"] - base["completed"]
     out = {"metric": "serve frames/s & p99 latency per resolution (4 resident scenes)",
            "value": round(done / elapsed, 2), "unit": "frames/s", "n_gpus": ws,
-           "higher_is_better": True, "dtype": "f16 products, f32 accumulate/blend" if args.precision == "fp16_tc" else "f32",
+           "higher_is_better": True, "dtype": DTYPE[args.precision],
            "data": "synthetic",
            "config": {"workload": "4 resident scenes of 200k/800k/1.5M/3M Gaussians (SH degree 3), "
                                   "Poisson arrivals, resolutions 640x480/1280x720/1920x1080/4096x2048",
@@ -295,7 +297,7 @@ TRAFFIC = {("k_raster_tc", "2x2"): {"bytes": 74296832,
 
 
 def _kernel_sources_sha1(kernel):
-    files = {"k_raster_tc": ["raster_tc.cu", "tgs_internal.cuh"],
+    files = {"k_raster_tc": ["raster_tc_impl.cuh", "tgs_internal.cuh"],
              "k_raster_fp32": ["raster_fp32.cu", "tgs_internal.cuh"]}[kernel]
     h = hashlib.sha1()
     for f in files:  # code only: comments and blank lines do not change the kernel
@@ -329,7 +331,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tgs", choices=["tgs", "reference"])
-    ap.add_argument("--precision", default="fp16_tc", choices=["fp16_tc", "fp32"])
+    ap.add_argument("--precision", default="fp16_tc", choices=["fp16_tc", "bf16_tc", "fp32"])
     ap.add_argument("--tiling", default="2x2")
     ap.add_argument("--splats", type=int, default=1_500_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -367,7 +369,7 @@ def main():
     rend = tgs.Renderer(ds, cams, tiling, args.precision)
     rend32 = tgs.Renderer(ds, cams, (1, 1), "fp32")  # the plain tile rasterizer, 1x1 tiles
     # ablation: the same tensor-core path without the exact (Gaussian, tile) skip
-    rend_nc = tgs.Renderer(ds, cams, tiling, args.precision, cull=False) if args.precision == "fp16_tc" else None
+    rend_nc = tgs.Renderer(ds, cams, tiling, args.precision, cull=False) if args.precision != "fp32" else None
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
     def timed(r, steps, warmup):
@@ -504,7 +506,7 @@ def main():
     # one evaluated pair costs the plain algorithm one ex2 on the special-function units, the
     # scarcest unit it uses, so the pair rate is bounded by the MUFU ex2 rate
     achieved = pairs / (raster_avg_ms * 1e-3) / 1e9
-    kernel = "k_raster_tc" if args.precision == "fp16_tc" else "k_raster_fp32"
+    kernel = "k_raster_tc" if args.precision != "fp32" else "k_raster_fp32"
     roofline = {"bound": "alu", "kernel": kernel,
                 "achieved": round(achieved, 2), "peak": round(mufu_peak, 1), "unit": "Gpair/s",
                 "frac": round(achieved / mufu_peak, 4), "traffic": _traffic(kernel, args),
@@ -521,7 +523,7 @@ def main():
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": "f16 products, f32 accumulate/blend" if args.precision == "fp16_tc" else "f32",
+           "dtype": DTYPE[args.precision],
            "data": "synthetic", "config": _config(scene, cams, args),
            "frame_ms": {"mean": round(float(frames_ms.mean()), 4), "p50": round(float(np.percentile(frames_ms, 50)), 4),
                         "p99": round(float(np.percentile(frames_ms, 99)), 4)},

@@ -55,6 +55,8 @@ typedef int32_t tgs_status;
 /* Precision of the rasterizer's exponent evaluation (the "power" of Eq. power). */
 #define TGS_PRECISION_FP32 0    /* scalar FP32 on the CUDA cores (the plain tile rasterizer) */
 #define TGS_PRECISION_FP16_TC 1 /* FP16 x FP16 -> FP32 product on the tensor cores (tcgen05) */
+#define TGS_PRECISION_BF16_TC 2 /* BF16 x BF16 -> FP32 product on the tensor cores (tcgen05), the
+                                   coefficients split three ways over K = 32 */
 
 typedef struct {
   int64_t n;              /* number of Gaussians */

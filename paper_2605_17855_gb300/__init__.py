@@ -24,7 +24,7 @@ import torch
 from . import build as _build
 
 TILE = 16
-PRECISION = {"fp32": 0, "fp16_tc": 1}
+PRECISION = {"fp32": 0, "fp16_tc": 1, "bf16_tc": 2}
 
 TGS_OK = 0
 TGS_ERR_INVALID_ARGUMENT = 1

@@ -194,6 +194,7 @@ tgs_status tgs_rasterize(const tgs_projected* proj, int64_t n, const tgs_bins* b
       return launch_raster_fp32(*proj, *bins, width, height, tiling->group_w, tiling->group_h,
                                 *opts, out_rgb, out_T, n_contrib, st);
     case TGS_PRECISION_FP16_TC:
+    case TGS_PRECISION_BF16_TC:
       return launch_raster_tc(*proj, *bins, width, height, tiling->group_w, tiling->group_h, *opts,
                               out_rgb, out_T, n_contrib, st);
     default:

@@ -1,700 +1,15 @@
-// Grouped tensor-core rasterizer (Section 4.2 "Tensorizing the power computation" and Section 4.4.2
-// "Grouped rasterization"; Algorithm 1, the per-group CTA loop), written for sm_103a with tcgen05.
-//
-// One CTA per tile group. The group's depth-sorted list is consumed in chunks of NB = 32 entries:
-//   * producer warps (several, on interleaved chunks): gather the chunk's Gaussians (mean, conic,
-//     opacity, colour, mask). For every member tile, the entries whose mask bit is set are packed
-//     to the front (Section 4.4.2: "select Gaussian entries whose bit mask includes t"), and for
-//     each the producer writes the Gaussian's coefficient row of the power expansion about the
-//     tile's centre (o_x, o_y) = (16 tx + 8, 16 ty + 8). With pixel offsets (x, y) = (px - o_x,
-//     py - o_y) and (mx, my) = mu' - o:
-//        log2(o) + log2(e) * power = q . [x^2, xy, y^2, x, y, 1]
-//        q = log2(e) * (-a/2, -b, -c/2, a mx + b my, b mx + c my, -(a mx^2 + 2 b mx my + c my^2)/2)
-//            + (0, 0, 0, 0, 0, log2 o)
-//     This is the expansion of Eq. tensorgs_power_scalar about a common origin, which makes the
-//     power a true matrix product (the Q Phi of Section 4.2.2 with the per-pixel terms separated
-//     from the per-Gaussian ones). q is split into FP16 hi + lo and the K dimension holds
-//     [hi(6), lo(6), 0, 0, 0, 0] against features [f(6), f(6), 0, 0, 0, 0]: the zero padding of
-//     Section 4.2.3 (exact), with the padding slots used for the lo half. |x|, |y| <= 8, so every
-//     feature is an exact FP16 integer. Rows whose FP16 error bound is too large take a scalar
-//     FP32 path in the epilogue instead. The producers are software-pipelined two chunks deep.
-//     Unless disabled, a producer also leaves out of a tile's packed rows every entry whose exact
-//     maximum exponent over the tile's 16x16 pixel centres is below log2(1/255) by a margin (the
-//     minimum of the conic's quadratic form over a box, in closed form): such an entry fails the
-//     pruning test at every pixel of the tile, so the image is unchanged; the tile's MMA rows,
-//     exponent loads and tests for it are saved (a 3-sigma AABB overlaps many tiles the Gaussian
-//     cannot reach at alpha >= 1/255).
-//   * MMA thread: per tile, D[128 px x 32] = A_h[128 x 16] * B_t[32 x 16]^T with
-//     tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 32, K = 16), FP32 accumulators in tensor
-//     memory, double-buffered; completion signalled through tcgen05.commit on mbarriers.
-//   * epilogue warpgroups (one per tile of a round): each thread owns one TMEM lane = one pixel in
-//     each of the tile's two 128-pixel M blocks, streams the tile's exponents out of tensor memory
-//     8 columns at a time (the next load in flight while the current columns are blended) and runs
-//     the front-to-back blend of Section 2 in FP32: skip if alpha < 1/255 (tested in the log2
-//     domain before the exp), alpha = min(0.99, 2^D), stop when T' < 1e-4 without blending.
-// The chunk is loaded from global memory once per group and reused by all member tiles
-// (the cross-tile reuse of Section 4.4.2); packing a tile's entries keeps their order, hence each
-// tile's front-to-back order (Section 4.4.2, numerical equivalence with per-tile rasterization).
-// Termination: before each chunk the MMA thread checks whether every epilogue warp has finished
-// all its pixels (T < 1e-4 or end of list); if so it stops issuing, raises a stop flag for the
-// producers and signals the epilogue the index of the last job.
-// Every wait on an mbarrier is bounded (2 s); on expiry the CTA records TGS_ERR_TIMEOUT in the
-// device error word, drains its MMAs, frees its tensor memory and exits.
-#include <algorithm>
-
-#include "tgs_internal.cuh"
+// Tensor-core rasterizer, FP16 operands (hi + lo coefficient split in one K block of 16), and the
+// dispatch to the BF16 variant. The kernel itself is in raster_tc_impl.cuh.
+#include "raster_tc_impl.cuh"
 
 namespace tgs {
-namespace {
-
-constexpr uint64_t kWaitLimitNs = 2000000000ull;
-constexpr float kL255 = -7.994353436858858f;            // log2(1/255)
-constexpr float kLog2AlphaMax = -0.014499569695115089f;  // log2(0.99)
-// Rows whose FP16 hi/lo error bound 2^-22 * sum_k |q_k| max|f_k| exceeds this (in log2 units)
-// are evaluated by the scalar FP32 path.
-constexpr float kMaxWeightedCoef = 4096.0f;
-// A (Gaussian, tile) pair is skipped when the largest exponent over the tile's pixel box is below
-// log2(1/255) by more than this (log2 units), far above the FP16 exponent error.
-constexpr float kCullMargin = 0.01f;
-constexpr int kLBO = 128;  // bytes between the two K core matrices of an 8-row group
-constexpr int kSBO = 256;  // bytes between 8-row groups
-constexpr int NB = 32;     // list entries per chunk = MMA N
-
-__device__ __forceinline__ float inf_f() { return __int_as_float(0x7f800000); }
-
-template <int GW, int GH, int NWG, int NPROD>
-struct Cfg {
-  static constexpr int kTiles = GW * GH;
-  static constexpr int kRounds = kTiles / NWG;
-  static_assert(kTiles % NWG == 0, "tiles must split evenly over warpgroups");
-  static constexpr int kEpiWarps = 4 * NWG;
-  static constexpr int kProdWarp0 = kEpiWarps;
-  static constexpr int kMmaWarp = kEpiWarps + NPROD;
-  static constexpr int kThreads = 32 * (kMmaWarp + 1);
-  static constexpr int kSlots = 2 * NPROD;  // chunk c uses slot c % kSlots, produced by c % NPROD
-  static constexpr int kStageCols = NWG * 2 * NB;
-  static constexpr int kTmemCols = 2 * kStageCols;
-  static_assert(kTmemCols == 32 || kTmemCols == 64 || kTmemCols == 128 || kTmemCols == 256 ||
-                    kTmemCols == 512,
-                "TMEM allocation must be a power of two in [32, 512]");
-};
-
-template <int TILES>
-struct __align__(16) Slot {
-  uint8_t B[TILES][NB * 32];  // per tile, packed rows; K-major canonical, no swizzle:
-                              // (row/8)*256 + (k/8)*128 + (row%8)*16
-  float4 rgbc[TILES][NB];     // packed entry k of tile t: colour, min(log2 o, log2 0.99)
-  float4 sp0[NB];             // chunk entry: mu'x, mu'y, l11, l12 (scalar rows; conic factor)
-  float2 sp1[NB];             // l22, log2 o
-  uint8_t entry[TILES][NB];   // chunk entry (0..31) of packed entry k of tile t
-  uint32_t cnt[TILES];        // packed entries of tile t
-  uint32_t sbits[TILES];      // bit k: packed entry k of tile t uses the scalar path
-  int32_t base;               // list position of chunk entry 0 relative to the group start
-};
-
-template <int TILES, int SLOTS>
-struct __align__(1024) Smem {
-  uint8_t A[2][4096];  // two 128-pixel M blocks of the tile feature operand
-  Slot<TILES> slot[SLOTS];
-  uint64_t full[SLOTS], empty[SLOTS], tfull[2], tempty[2], drain;
-  uint32_t tmem_base;
-  int abort;       // a bounded wait expired somewhere in the CTA
-  int stop;        // the MMA thread stopped issuing: producers quit
-  int end_job;     // index of the job whose tfull phase signals the end (-1 until known)
-  int done_warps;  // epilogue warps whose pixels have all finished
-};
-
-// Pixel of TMEM lane m (0..127) of M block h inside a 16x16 tile: warp quarters are 8x4 pixels.
-__device__ __forceinline__ void lane_pixel(int h, int m, int& lx, int& ly) {
-  const int bi = h * 4 + (m >> 5), l = m & 31;
-  lx = (bi & 1) * 8 + (l & 7);
-  ly = (bi >> 1) * 4 + (l >> 3);
-}
-
-__device__ __forceinline__ uint32_t pack_h2(float lo_elem, float hi_elem) {
-  const __half2 h = __floats2half2_rn(lo_elem, hi_elem);
-  return *reinterpret_cast<const uint32_t*>(&h);
-}
-
-__device__ __forceinline__ void record_abort(int* abort_flag, int32_t* err) {
-  *reinterpret_cast<volatile int*>(abort_flag) = 1;
-  if (err) atomicExch(err, TGS_ERR_TIMEOUT);
-}
-
-// Blend state of one pixel. `thr` is log2(1/255) while the pixel is live and +inf once it has
-// terminated, so the pruning test alone also skips finished pixels.
-struct PixState {
-  float T, r, g, b, thr;
-  int last;
-};
-
-// Smallest value of the quadratic form Q(d) = d^T conic d over the box of offsets
-// d in [dx0, dx1] x [dy0, dy1] (the pixel centres of a tile relative to the Gaussian's mean). Q is
-// convex: its minimum is 0 if the box holds d = 0, else it lies on an edge, where the 1D minimum is
-// at the clamped stationary point. Evaluated through the Cholesky factor, Q = (l11 dx + l12 dy)^2 +
-// (l22 dy)^2, so the result is a sum of squares.
-__device__ __forceinline__ float box_min_quadratic(float a, float b, float c, float3 L, float dx0,
-                                                   float dx1, float dy0, float dy1) {
-  if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return 0.f;
-  auto q = [&](float dx, float dy) {
-    const float u = fmaf(L.x, dx, L.y * dy), v = L.z * dy;
-    return fmaf(u, u, v * v);
-  };
-  const float ia = 1.f / a, ic = 1.f / c;
-  float m = q(dx0, fminf(fmaxf(-b * dx0 * ic, dy0), dy1));
-  m = fminf(m, q(dx1, fminf(fmaxf(-b * dx1 * ic, dy0), dy1)));
-  m = fminf(m, q(fminf(fmaxf(-b * dy0 * ia, dx0), dx1), dy0));
-  m = fminf(m, q(fminf(fmaxf(-b * dy1 * ia, dx0), dx1), dy1));
-  return m;
-}
-
-// Scalar FP32 exponents of a packed entry whose FP16 coefficients would be too inaccurate.
-__device__ __noinline__ float2 scalar_exponents(float px0, float py0, float px1, float py1,
-                                                float4 p0, float2 p1) {
-  const float3 L = make_float3(p0.z, p0.w, p1.x);
-  const float e0 = fmaf(power_fp32(L, __fsub_rn(px0, p0.x), __fsub_rn(py0, p0.y)), kLog2e, p1.y);
-  const float e1 = fmaf(power_fp32(L, __fsub_rn(px1, p0.x), __fsub_rn(py1, p0.y)), kLog2e, p1.y);
-  return make_float2(e0, e1);
-}
-
-// One front-to-back step (Section 2) for one pixel, branch-free: the pruning test against the
-// pixel's live threshold predicates the update. D = log2(o e^power) already contains the opacity,
-// so alpha = min(0.99, 2^D) = 2^min(D, log2 0.99). NC: track the last blended list position.
-template <bool COUNT, bool NC>
-__device__ __forceinline__ void blend_step(float e, const float4& rc, PixState& s, int pos,
-                                           unsigned long long& passing) {
-  const bool p = e >= s.thr;                 // alpha >= 1/255 and the pixel is live
-  if (COUNT) passing += p;
-  const float a = ex2(fminf(e, kLog2AlphaMax));
-  const float Tn = fmaf(-s.T, a, s.T);       // T (1 - alpha)
-  const bool term = p && (Tn < kTMin);       // early termination: this entry is not blended
-  if (p && !term) {
-    const float w = a * s.T;
-    s.r = fmaf(w, rc.x, s.r);
-    s.g = fmaf(w, rc.y, s.g);
-    s.b = fmaf(w, rc.z, s.b);
-    s.T = Tn;
-    if (NC) s.last = pos;
-  }
-  if (term) s.thr = inf_f();
-}
-
-// One packed entry (column jj of granule g) blended into the thread's two pixels.
-template <int TILES, bool COUNT, bool NC>
-__device__ __forceinline__ void blend_column(float e0, float e1, int j, int base,
-                                             const Slot<TILES>& sl, int t, PixState& s0,
-                                             PixState& s1, unsigned long long& evaluated,
-                                             unsigned long long& passing) {
-  if (COUNT) evaluated += (s0.thr < inf_f()) + (s1.thr < inf_f());
-  const float4 rc = sl.rgbc[t][j];
-  const int pos = NC ? base + (int)sl.entry[t][j] + 1 : 0;
-  blend_step<COUNT, NC>(e0, rc, s0, pos, passing);
-  blend_step<COUNT, NC>(e1, rc, s1, pos, passing);
-}
-
-// Blends one 8-column granule (packed entries 8g .. 8g+7 of tile t) into the thread's two pixels.
-// d[0..7] are pixel 0's exponents, d[8..15] pixel 1's. The steps are predicated, not branched per
-// column, so the exponentials and tests of different columns and pixels overlap; a granule that
-// is cut by the end of the tile's packed entries only runs its valid columns.
-template <int TILES, bool COUNT, bool NC>
-__device__ __forceinline__ void blend_granule(const uint32_t (&d)[16], int g, int cnt, uint32_t sb,
-                                              int base, const Slot<TILES>& sl, int t, int tx,
-                                              int ty, int quarter, int lane, PixState& s0,
-                                              PixState& s1, unsigned long long& evaluated,
-                                              unsigned long long& passing,
-                                              unsigned long long& slots) {
-  if (COUNT) slots += 16;
-  float e0[8], e1[8];
-#pragma unroll
-  for (int jj = 0; jj < 8; ++jj) {
-    e0[jj] = __uint_as_float(d[jj]);
-    e1[jj] = __uint_as_float(d[8 + jj]);
-  }
-  const uint32_t sbg = (sb >> (8 * g)) & 0xffu;
-  if (sbg) {  // rare: rows whose FP16 coefficients would be too inaccurate
-    int lx0, ly0, lx1, ly1;
-    lane_pixel(0, quarter * 32 + lane, lx0, ly0);
-    lane_pixel(1, quarter * 32 + lane, lx1, ly1);
-    const float px0 = (float)(tx * kTile + lx0), py0 = (float)(ty * kTile + ly0);
-    const float px1 = (float)(tx * kTile + lx1), py1 = (float)(ty * kTile + ly1);
-#pragma unroll
-    for (int jj = 0; jj < 8; ++jj)
-      if ((sbg >> jj) & 1u) {
-        const int en = sl.entry[t][8 * g + jj];
-        const float2 es = scalar_exponents(px0, py0, px1, py1, sl.sp0[en], sl.sp1[en]);
-        e0[jj] = es.x;
-        e1[jj] = es.y;
-      }
-  }
-  const int ncols = cnt - 8 * g;  // >= 1; warp-uniform
-  if (ncols >= 8) {
-#pragma unroll
-    for (int jj = 0; jj < 8; ++jj)
-      blend_column<TILES, COUNT, NC>(e0[jj], e1[jj], 8 * g + jj, base, sl, t, s0, s1, evaluated,
-                                     passing);
-  } else {
-#pragma unroll
-    for (int jj = 0; jj < 7; ++jj)
-      if (jj < ncols)
-        blend_column<TILES, COUNT, NC>(e0[jj], e1[jj], 8 * g + jj, base, sl, t, s0, s1, evaluated,
-                                       passing);
-  }
-}
-
-template <int GW, int GH, int NWG, int NPROD, bool COUNT, bool NC>
-__global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD>::kThreads, 1)
-    k_raster_tc(const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ vals,
-                const uint16_t* __restrict__ masks, const float2* __restrict__ mean2d,
-                const float4* __restrict__ conic_opacity, const float* __restrict__ rgb, int width,
-                int height, int GX, float3 bg, float* __restrict__ out_rgb,
-                float* __restrict__ out_T, int* __restrict__ n_contrib,
-                unsigned long long* __restrict__ counters, int32_t* __restrict__ err, int cull) {
-  using C = Cfg<GW, GH, NWG, NPROD>;
-  constexpr int TILES = C::kTiles;
-  constexpr int SLOTS = C::kSlots;
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
-  auto& S = *reinterpret_cast<Smem<TILES, SLOTS>*>(smem_raw);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gid = blockIdx.x;
-  const int gx = gid % GX, gy = gid / GX;
-
-  // ---- set-up: feature operand A, barriers, tensor memory -------------------------------------
-  for (int m = threadIdx.x; m < 256; m += blockDim.x) {
-    const int h = m >> 7, row = m & 127;
-    int lx, ly;
-    lane_pixel(h, row, lx, ly);
-    const float x = (float)(lx - 8), y = (float)(ly - 8);
-    const float f[6] = {x * x, x * y, y * y, x, y, 1.f};
-    uint4 c0, c1;
-    c0.x = pack_h2(f[0], f[1]); c0.y = pack_h2(f[2], f[3]); c0.z = pack_h2(f[4], f[5]);
-    c0.w = pack_h2(f[0], f[1]);
-    c1.x = pack_h2(f[2], f[3]); c1.y = pack_h2(f[4], f[5]); c1.z = 0u; c1.w = 0u;
-    uint8_t* rowp = &S.A[h][(row >> 3) * kSBO + (row & 7) * 16];
-    *reinterpret_cast<uint4*>(rowp) = c0;
-    *reinterpret_cast<uint4*>(rowp + kLBO) = c1;
-  }
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < SLOTS; ++s) {
-      mbar_init(&S.full[s], 1);
-      mbar_init(&S.empty[s], C::kEpiWarps + 1);
-    }
-    for (int s = 0; s < 2; ++s) {
-      mbar_init(&S.tfull[s], 1);
-      mbar_init(&S.tempty[s], C::kEpiWarps);
-    }
-    mbar_init(&S.drain, 1);
-    S.abort = 0;
-    S.stop = 0;
-    S.end_job = -1;
-    S.done_warps = 0;
-    fence_mbarrier_init();
-  }
-  if (warp == C::kMmaWarp) {
-    tmem_alloc(&S.tmem_base, C::kTmemCols);
-    tmem_relinquish();
-  }
-  fence_proxy_async_smem();
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = S.tmem_base;
-  volatile int* abort_flag = &S.abort;
-  volatile int* stop_flag = &S.stop;
-
-  const uint32_t list_start = ranges[2 * gid], list_end = ranges[2 * gid + 1];
-  const int nchunks = (int)((list_end - list_start + NB - 1) / NB);
-
-  if (warp >= C::kProdWarp0 && warp < C::kMmaWarp) {
-    // ---- producers: gather, pack per tile, coefficient rows; chunks c = p, p + NPROD, ... -------
-    // Software pipeline, two chunks deep: while chunk c is packed, the Gaussian gathers of chunk
-    // c + NPROD and the index/mask loads of chunk c + 2 NPROD are in flight.
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    auto load_index = [&](int c, uint32_t& idx, uint32_t& msk, bool& valid) {
-      const uint32_t e = list_start + (uint32_t)c * NB + lane;
-      valid = c < nchunks && e < list_end;
-      idx = valid ? vals[e] : 0u;
-      msk = valid ? (uint32_t)masks[e] : 0u;
-    };
-    struct Gathered {
-      float2 mu;
-      float4 co;
-      float3 col;
-    };
-    auto gather = [&](uint32_t idx, bool valid, Gathered& g) {
-      g.mu = valid ? mean2d[idx] : make_float2(0.f, 0.f);
-      g.co = valid ? conic_opacity[idx] : make_float4(0.f, 0.f, 0.f, 1.f);
-      g.col = valid ? make_float3(rgb[3 * idx], rgb[3 * idx + 1], rgb[3 * idx + 2])
-                    : make_float3(0.f, 0.f, 0.f);
-    };
-    int c = warp - C::kProdWarp0;
-    uint32_t idx_a, msk_a, idx_b, msk_b;
-    bool val_a, val_b;
-    load_index(c, idx_a, msk_a, val_a);
-    Gathered g_a;
-    gather(idx_a, val_a, g_a);
-    load_index(c + NPROD, idx_b, msk_b, val_b);
-    for (; c < nchunks; c += NPROD) {
-      Gathered g_b;
-      gather(idx_b, val_b, g_b);  // chunk c + NPROD
-      uint32_t idx_c, msk_c;
-      bool val_c;
-      load_index(c + 2 * NPROD, idx_c, msk_c, val_c);
-      const int s = c % SLOTS;
-      const int w = mbar_wait_or_stop(&S.empty[s], ((c / SLOTS) & 1) ^ 1, stop_flag, abort_flag,
-                                      kWaitLimitNs);
-      const unsigned wmax = __reduce_max_sync(0xffffffffu, (unsigned)w);
-      if (wmax != 0u) {  // stopped (not an error) or timed out
-        if (wmax == 2u) record_abort(&S.abort, err);
-        break;
-      }
-      auto& sl = S.slot[s];
-      const bool valid = val_a;
-      const uint32_t msk = msk_a;
-      const float2 mu = g_a.mu;
-      const float4 co = g_a.co;
-      const float lo2 = lg2(co.w);
-      // Cholesky factor of the conic (used for the linear/constant terms and the scalar rows);
-      // here from the hardware reciprocal square root, the determinant by Kahan's scheme
-      float3 Lc = make_float3(0.f, 0.f, 0.f);
-      if (valid) {
-        const float inv = rsqrtf(co.x);
-        const float w2 = co.y * co.y;
-        const float det = fmaf(co.x, co.z, -w2) + fmaf(-co.y, co.y, w2);
-        const float dp = fmaxf(det, 0.f);
-        Lc = make_float3(co.x * inv, co.y * inv, dp > 0.f ? dp * rsqrtf(dp) * inv : 0.f);
-      }
-      const float4 rgbc = make_float4(g_a.col.x, g_a.col.y, g_a.col.z, fminf(lo2, kLog2AlphaMax));
-      sl.sp0[lane] = make_float4(mu.x, mu.y, Lc.x, Lc.y);
-      sl.sp1[lane] = make_float2(Lc.z, lo2);
-#pragma unroll
-      for (int t = 0; t < TILES; ++t) {
-        const int tx = gx * GW + (t % GW), ty = gy * GH + (t / GW);
-        bool active = valid && ((msk >> t) & 1u);
-        if (active && cull) {
-          // skip the pair if no pixel of the tile can reach alpha >= 1/255 (exact bound)
-          const float mx = mu.x - (float)(tx * kTile), my = mu.y - (float)(ty * kTile);
-          const float qmin = box_min_quadratic(co.x, co.y, co.z, Lc, -mx, 15.f - mx, -my, 15.f - my);
-          active = fmaf(-0.5f * kLog2e, qmin, lo2) >= kL255 - kCullMargin;
-        }
-        const uint32_t bal = __ballot_sync(0xffffffffu, active);
-        const uint32_t cnt_t = __popc(bal);
-        // active entries are packed to rows 0..cnt-1 in list order; the other lanes fill rows
-        // cnt..31 with a row whose exponent never passes the pruning test
-        const uint32_t pos = active ? __popc(bal & lt_mask) : cnt_t + __popc(~bal & lt_mask);
-        bool scalar = false;
-        uint4 r0 = make_uint4(0u, 0u, 0u, 0u), r1 = make_uint4(0u, 0u, 0u, 0u);
-        if (!active) r0.z = pack_h2(0.f, -30000.f);  // constant term of the padding rows
-        if (active) {
-          const float mx = mu.x - (float)(tx * kTile + 8), my = mu.y - (float)(ty * kTile + 8);
-          // (u, v) = L m: the linear and constant terms are formed from it (conic m = L^T L m and
-          // m^T conic m = u^2 + v^2), which avoids the cancellation of the expanded products when
-          // the tile is far from the centre of a thin splat
-          const float u = fmaf(Lc.x, mx, Lc.y * my), v = Lc.z * my;
-          float q[6];
-          q[0] = -0.5f * co.x * kLog2e;
-          q[1] = -co.y * kLog2e;
-          q[2] = -0.5f * co.z * kLog2e;
-          q[3] = Lc.x * u * kLog2e;
-          q[4] = fmaf(Lc.y, u, Lc.z * v) * kLog2e;
-          q[5] = fmaf(-0.5f * kLog2e, fmaf(u, u, v * v), lo2);
-          const float wsum = 64.f * (fabsf(q[0]) + fabsf(q[1]) + fabsf(q[2])) +
-                             8.f * (fabsf(q[3]) + fabsf(q[4])) + fabsf(q[5]);
-          scalar = !(wsum <= kMaxWeightedCoef);
-          if (!scalar) {
-            const __half2 h01 = __floats2half2_rn(q[0], q[1]), h23 = __floats2half2_rn(q[2], q[3]),
-                          h45 = __floats2half2_rn(q[4], q[5]);
-            const float2 f01 = __half22float2(h01), f23 = __half22float2(h23),
-                         f45 = __half22float2(h45);
-            r0.x = *reinterpret_cast<const uint32_t*>(&h01);
-            r0.y = *reinterpret_cast<const uint32_t*>(&h23);
-            r0.z = *reinterpret_cast<const uint32_t*>(&h45);
-            r0.w = pack_h2(q[0] - f01.x, q[1] - f01.y);
-            r1.x = pack_h2(q[2] - f23.x, q[3] - f23.y);
-            r1.y = pack_h2(q[4] - f45.x, q[5] - f45.y);
-          }
-          sl.rgbc[t][pos] = rgbc;
-          sl.entry[t][pos] = (uint8_t)lane;
-        }
-        uint8_t* rowp = &sl.B[t][(pos >> 3) * kSBO + (pos & 7) * 16];
-        *reinterpret_cast<uint4*>(rowp) = r0;
-        *reinterpret_cast<uint4*>(rowp + kLBO) = r1;
-        const uint32_t sb = __reduce_or_sync(0xffffffffu, (active && scalar) ? (1u << pos) : 0u);
-        if (lane == 0) {
-          sl.cnt[t] = cnt_t;
-          sl.sbits[t] = sb;
-        }
-      }
-      if (lane == 0) sl.base = c * NB;
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&S.full[s]);
-      // rotate the pipeline
-      g_a = g_b;
-      msk_a = msk_b;
-      val_a = val_b;
-      idx_b = idx_c;
-      msk_b = msk_c;
-      val_b = val_c;
-    }
-  } else if (warp == C::kMmaWarp) {
-    // ---- MMA issuer ---------------------------------------------------------------------------
-    if (lane == 0) {
-      constexpr uint32_t idesc = idesc_f16(128, NB, false);
-      const uint64_t adesc0 = smem_desc(smem_addr(&S.A[0][0]), kLBO, kSBO);
-      const uint64_t adesc1 = smem_desc(smem_addr(&S.A[1][0]), kLBO, kSBO);
-      int job = 0;
-      bool failed = false;
-      for (int c = 0; c < nchunks && !failed; ++c) {
-        // every epilogue warp has finished all its pixels: no more work for this group
-        if (*reinterpret_cast<volatile int*>(&S.done_warps) >= C::kEpiWarps) break;
-        const int s = c % SLOTS;
-        if (!mbar_wait_bounded(&S.full[s], (c / SLOTS) & 1, abort_flag, kWaitLimitNs)) {
-          failed = true;
-          break;
-        }
-        auto& sl = S.slot[s];
-        for (int r = 0; r < C::kRounds; ++r, ++job) {
-          const int st = job & 1;
-          if (!mbar_wait_bounded(&S.tempty[st], ((job >> 1) & 1) ^ 1, abort_flag, kWaitLimitNs)) {
-            failed = true;
-            break;
-          }
-          tc_fence_after();
-#pragma unroll
-          for (int g = 0; g < NWG; ++g) {
-            const int t = g + NWG * r;
-            if (sl.cnt[t] == 0u) continue;
-            const uint64_t bdesc = smem_desc(smem_addr(&sl.B[t][0]), kLBO, kSBO);
-            const uint32_t col = (uint32_t)(st * C::kStageCols + (2 * g) * NB);
-            mma_f16(tmem + col, adesc0, bdesc, idesc, 0u);
-            mma_f16(tmem + col + NB, adesc1, bdesc, idesc, 0u);
-          }
-          mma_commit(&S.tfull[st]);
-        }
-        if (!failed) mma_commit(&S.empty[s]);
-      }
-      *stop_flag = 1;
-      if (failed) {
-        record_abort(&S.abort, err);
-      } else {
-        // end signal: complete the next tfull phase with a plain arrive after publishing its index
-        const int st = job & 1;
-        if (mbar_wait_bounded(&S.tempty[st], ((job >> 1) & 1) ^ 1, abort_flag, kWaitLimitNs)) {
-          *reinterpret_cast<volatile int*>(&S.end_job) = job;
-          mbar_arrive(&S.tfull[st]);
-        } else {
-          record_abort(&S.abort, err);
-        }
-      }
-      // drain: all MMAs issued by this thread have completed before tensor memory is freed
-      mma_commit(&S.drain);
-      if (!mbar_wait_bounded(&S.drain, 0, abort_flag, kWaitLimitNs)) record_abort(&S.abort, err);
-    }
-    __syncwarp();
-  } else {
-    // ---- epilogue warpgroups ------------------------------------------------------------------
-    const int wg = warp >> 2, quarter = warp & 3;
-    PixState ps[C::kRounds][2];
-    bool wdone[C::kRounds];
-#pragma unroll
-    for (int r = 0; r < C::kRounds; ++r) {
-      const int t = wg + NWG * r;
-      const int tx = gx * GW + (t % GW), ty = gy * GH + (t / GW);
-      bool all = true;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        int lx, ly;
-        lane_pixel(h, quarter * 32 + lane, lx, ly);
-        const bool inside = tx * kTile + lx < width && ty * kTile + ly < height;
-        ps[r][h] = PixState{1.f, 0.f, 0.f, 0.f, inside ? kL255 : inf_f(), 0};
-        all &= !inside;
-      }
-      wdone[r] = __all_sync(0xffffffffu, all);
-    }
-    bool counted_done = false;
-    unsigned long long evaluated = 0, passing = 0, slots = 0;
-    int job = 0;
-    bool finished = false;
-    for (int c = 0; !finished; ++c) {
-      const int s = c % SLOTS;
-#pragma unroll
-      for (int r = 0; r < C::kRounds; ++r) {
-        const int st = job & 1;
-        bool ok = mbar_wait_bounded(&S.tfull[st], (job >> 1) & 1, abort_flag, kWaitLimitNs);
-        if (!__all_sync(0xffffffffu, ok)) { record_abort(&S.abort, err); finished = true; break; }
-        if (__shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(&S.end_job), 0) == job) {
-          finished = true;
-          break;
-        }
-        if (r == 0) {
-          // the slot's producer writes (colours, packing) are complete: the MMA thread waited on
-          // the same phase before issuing this job
-          ok = mbar_wait_bounded(&S.full[s], (c / SLOTS) & 1, abort_flag, kWaitLimitNs);
-          if (!__all_sync(0xffffffffu, ok)) { record_abort(&S.abort, err); finished = true; break; }
-        }
-        ++job;
-        tc_fence_after();
-        const auto& sl = S.slot[s];
-        const int t = wg + NWG * r;
-        const int cnt = (int)sl.cnt[t];
-        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) +
-                               (uint32_t)(st * C::kStageCols + (2 * wg) * NB);
-        if (cnt > 0 && !wdone[r]) {
-          const uint32_t sb = sl.sbits[t];
-          const int base = sl.base;
-          const int tx = gx * GW + (t % GW), ty = gy * GH + (t / GW);
-          const int ngr = (cnt + 7) >> 3;  // 8-column granules holding the packed entries
-          uint32_t ga[16], gb[16];
-          __syncwarp();
-          tmem_ld8x2_async(taddr, taddr + NB, ga);
-          tmem_wait_ld(ga);
-          // granule g is blended while granule g + 1 is loading; the stage is released once its
-          // last load has completed
-          for (int g = 0; g < ngr; g += 2) {
-            if (g + 1 < ngr) {
-              __syncwarp();
-              tmem_ld8x2_async(taddr + 8 * (g + 1), taddr + NB + 8 * (g + 1), gb);
-            } else {
-              tc_fence_before();
-              __syncwarp();
-              if (lane == 0) mbar_arrive(&S.tempty[st]);
-            }
-            blend_granule<TILES, COUNT, NC>(ga, g, cnt, sb, base, sl, t, tx, ty, quarter, lane,
-                                        ps[r][0], ps[r][1], evaluated, passing, slots);
-            if (g + 1 < ngr) {
-              tmem_wait_ld(gb);
-              if (g + 2 < ngr) {
-                __syncwarp();
-                tmem_ld8x2_async(taddr + 8 * (g + 2), taddr + NB + 8 * (g + 2), ga);
-              } else {
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&S.tempty[st]);
-              }
-              blend_granule<TILES, COUNT, NC>(gb, g + 1, cnt, sb, base, sl, t, tx, ty, quarter, lane,
-                                          ps[r][0], ps[r][1], evaluated, passing, slots);
-              if (g + 2 < ngr) tmem_wait_ld(ga);
-            }
-          }
-          wdone[r] = __all_sync(0xffffffffu, ps[r][0].thr == inf_f() && ps[r][1].thr == inf_f());
-        } else {
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&S.tempty[st]);
-        }
-        if (r == C::kRounds - 1) {
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&S.empty[s]);
-        }
-      }
-      if (!finished && !counted_done) {
-        bool all = true;
-#pragma unroll
-        for (int r = 0; r < C::kRounds; ++r) all &= wdone[r];
-        if (all) {
-          counted_done = true;
-          if (lane == 0) atomicAdd(&S.done_warps, 1);
-        }
-      }
-    }
-    // ---- outputs ------------------------------------------------------------------------------
-    const size_t HW = (size_t)width * height;
-#pragma unroll
-    for (int r = 0; r < C::kRounds; ++r) {
-      const int t = wg + NWG * r;
-      const int tx = gx * GW + (t % GW), ty = gy * GH + (t / GW);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        int lx, ly;
-        lane_pixel(h, quarter * 32 + lane, lx, ly);
-        const int X = tx * kTile + lx, Y = ty * kTile + ly;
-        if (X >= width || Y >= height) continue;
-        const size_t p = (size_t)Y * width + X;
-        const PixState& q = ps[r][h];
-        out_rgb[p] = q.r + q.T * bg.x;
-        out_rgb[HW + p] = q.g + q.T * bg.y;
-        out_rgb[2 * HW + p] = q.b + q.T * bg.z;
-        out_T[p] = q.T;
-        if (n_contrib) n_contrib[p] = q.last;
-      }
-    }
-    if (COUNT) {
-      for (int o = 16; o > 0; o >>= 1) {
-        evaluated += __shfl_xor_sync(0xffffffffu, evaluated, o);
-        passing += __shfl_xor_sync(0xffffffffu, passing, o);
-        slots += __shfl_xor_sync(0xffffffffu, slots, o);
-      }
-      if (lane == 0) {
-        if (evaluated) atomicAdd(counters, evaluated);
-        if (passing) atomicAdd(counters + 1, passing);
-        if (slots) atomicAdd(counters + 2, slots);
-      }
-    }
-  }
-
-  // ---- teardown -----------------------------------------------------------------------------
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (warp == C::kMmaWarp) tmem_dealloc(tmem, C::kTmemCols);
-}
-
-template <int GW, int GH, int NWG, int NPROD>
-tgs_status launch_cfg(const tgs_projected& p, const tgs_bins& b, int width, int height,
-                      const tgs_raster_opts& o, float* out_rgb, float* out_T, int32_t* n_contrib,
-                      cudaStream_t st) {
-  using Cf = Cfg<GW, GH, NWG, NPROD>;
-  using Sm = Smem<GW * GH, Cf::kSlots>;
-  const int TX = div_up(width, kTile), TY = div_up(height, kTile);
-  const int GX = div_up(TX, GW), GY = div_up(TY, GH);
-  // Limit residency so that co-resident CTAs never wait on each other's tensor memory:
-  // at most 512 / kTmemCols CTAs per SM.
-  int dev = 0, smem_sm = 0;
-  TGS_CUDA(cudaGetDevice(&dev));
-  TGS_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-  const int max_ctas = 512 / Cf::kTmemCols;
-  size_t smem = sizeof(Sm) + 1024;  // + alignment slack
-  const size_t floor_bytes = (size_t)smem_sm / (max_ctas + 1) - 1024 + 16;
-  smem = std::max(smem, floor_bytes);
-  const bool count = o.counters != nullptr;
-  auto* m2 = reinterpret_cast<const float2*>(p.mean2d);
-  auto* co = reinterpret_cast<const float4*>(p.conic_opacity);
-  auto* cnt = reinterpret_cast<unsigned long long*>(o.counters);
-  const float3 bg = make_float3(o.bg[0], o.bg[1], o.bg[2]);
-  int32_t* err = device_error_word();
-  const int cull = (o.flags & TGS_RASTER_NO_CULL) ? 0 : 1;
-  auto launch = [&](auto* k) -> tgs_status {
-    TGS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k<<<GX * GY, Cf::kThreads, smem, st>>>(b.ranges, b.vals, b.masks, m2, co, p.rgb, width, height,
-                                           GX, bg, out_rgb, out_T, n_contrib, cnt, err, cull);
-    return TGS_OK;
-  };
-  tgs_status s;
-  if (count)
-    s = n_contrib ? launch(k_raster_tc<GW, GH, NWG, NPROD, true, true>)
-                  : launch(k_raster_tc<GW, GH, NWG, NPROD, true, false>);
-  else
-    s = n_contrib ? launch(k_raster_tc<GW, GH, NWG, NPROD, false, true>)
-                  : launch(k_raster_tc<GW, GH, NWG, NPROD, false, false>);
-  if (s != TGS_OK) return s;
-  TGS_CHECK_LAUNCH("k_raster_tc");
-  return TGS_OK;
-}
-
-}  // namespace
 
 tgs_status launch_raster_tc(const tgs_projected& p, const tgs_bins& b, int width, int height, int gw,
                             int gh, const tgs_raster_opts& o, float* out_rgb, float* out_T,
                             int32_t* n_contrib, cudaStream_t st) {
-  if (((uintptr_t)p.mean2d & 7) || ((uintptr_t)p.conic_opacity & 15))
-    return set_error("mean2d needs 8-byte and conic_opacity 16-byte alignment"), TGS_ERR_INVALID_ARGUMENT;
-  if (gw == 1 && gh == 1) return launch_cfg<1, 1, 1, 2>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
-  if (gw == 2 && gh == 2) return launch_cfg<2, 2, 4, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
-  if (gw == 4 && gh == 2) return launch_cfg<4, 2, 4, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
-  if (gw == 2 && gh == 4) return launch_cfg<2, 4, 4, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
-  if (gw == 4 && gh == 4) return launch_cfg<4, 4, 4, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
-  set_error("tensor-core path supports groups 1x1, 2x2, 4x2, 2x4, 4x4 (got %dx%d)", gw, gh);
-  return TGS_ERR_INVALID_ARGUMENT;
+  if (o.precision == TGS_PRECISION_BF16_TC)
+    return launch_raster_tc_bf16(p, b, width, height, gw, gh, o, out_rgb, out_T, n_contrib, st);
+  return launch_raster_tc_typed<false>(p, b, width, height, gw, gh, o, out_rgb, out_T, n_contrib, st);
 }
 
 }  // namespace tgs

@@ -48,6 +48,9 @@ tgs_status launch_raster_fp32(const tgs_projected& p, const tgs_bins& b, int wid
 tgs_status launch_raster_tc(const tgs_projected& p, const tgs_bins& b, int width, int height, int gw,
                             int gh, const tgs_raster_opts& o, float* out_rgb, float* out_T,
                             int32_t* n_contrib, cudaStream_t st);
+tgs_status launch_raster_tc_bf16(const tgs_projected& p, const tgs_bins& b, int width, int height, int gw,
+                            int gh, const tgs_raster_opts& o, float* out_rgb, float* out_T,
+                            int32_t* n_contrib, cudaStream_t st);
 tgs_status launch_raster_backward(const tgs_projected& p, int64_t n, const tgs_bins& b, int width,
                                   int height, int gw, int gh, const tgs_raster_opts& o,
                                   const float* out_T, const int32_t* n_contrib, const float* grad_rgb,

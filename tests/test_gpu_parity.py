@@ -196,10 +196,13 @@ def test_fp32_raster_parity(case, tiling):
     assert abs(ev - img.evaluated) <= 0.001 * img.evaluated + 10
 
 
-@pytest.mark.parametrize("tiling", [(1, 1), (2, 2), (4, 2), (2, 4), (4, 4)])
-def test_tc_raster_parity(case, tiling):
+@pytest.mark.parametrize("tiling,precision", [((1, 1), "fp16_tc"), ((2, 2), "fp16_tc"),
+                                              ((4, 2), "fp16_tc"), ((2, 4), "fp16_tc"),
+                                              ((4, 4), "fp16_tc"), ((1, 1), "bf16_tc"),
+                                              ((2, 2), "bf16_tc"), ((4, 4), "bf16_tc")])
+def test_tc_raster_parity(case, tiling, precision):
     name, scene, cam = case
-    rgb, T, nc, img, (ev, passing, _) = _raster_vs_oracle(scene, cam, tiling, "fp16_tc", counters=True)
+    rgb, T, nc, img, (ev, passing, _) = _raster_vs_oracle(scene, cam, tiling, precision, counters=True)
     ref = _chw(img.rgb)
     psnr = oracle.psnr(rgb, ref)
     assert psnr >= TC_PSNR, psnr
@@ -213,8 +216,9 @@ def test_tc_raster_parity(case, tiling):
     assert ev <= 1.01 * img.evaluated + 10
 
 
-@pytest.mark.parametrize("tiling", [(1, 1), (2, 2), (4, 4)])
-def test_tc_tile_cull_is_exact(case, tiling):
+@pytest.mark.parametrize("tiling,precision", [((1, 1), "fp16_tc"), ((2, 2), "fp16_tc"),
+                                              ((4, 4), "fp16_tc"), ((2, 2), "bf16_tc")])
+def test_tc_tile_cull_is_exact(case, tiling, precision):
     # Skipping (Gaussian, tile) pairs whose largest exponent over the tile is below log2(1/255) by
     # the margin removes only pairs the per-pixel test prunes: the image is bit-identical to the
     # image without the skip, and the pairs evaluated without it match the oracle's count.
@@ -223,7 +227,7 @@ def test_tc_tile_cull_is_exact(case, tiling):
     res = {}
     for cull in (True, False):
         cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
-        rgb, T, nc = tgs.rasterize(proj, bins, cam.width, cam.height, "fp16_tc", counters=cnt,
+        rgb, T, nc = tgs.rasterize(proj, bins, cam.width, cam.height, precision, counters=cnt,
                                    cull=cull)
         torch.cuda.synchronize()
         assert tgs.last_device_error() == 0
@@ -243,10 +247,10 @@ def test_grouping_is_exact_on_gpu(case):
     outs = {}
     for tiling in [(1, 1), (2, 2), (4, 2)]:
         _, proj, bins = _gpu_frame(scene, cam, tiling)
-        for prec in ("fp32", "fp16_tc"):
+        for prec in ("fp32", "fp16_tc", "bf16_tc"):
             rgb, T, _ = tgs.rasterize(proj, bins, cam.width, cam.height, prec, want_n_contrib=False)
             outs[(tiling, prec)] = (_np(rgb), _np(T))
-    for prec in ("fp32", "fp16_tc"):
+    for prec in ("fp32", "fp16_tc", "bf16_tc"):
         base = outs[((1, 1), prec)]
         for tiling in [(2, 2), (4, 2)]:
             assert np.array_equal(outs[(tiling, prec)][0], base[0]), (tiling, prec)
@@ -288,14 +292,15 @@ def test_background_blend():
     assert oracle.psnr(_np(rgb), _chw(img.rgb)) >= TC_PSNR
 
 
-def test_tc_scalar_fallback_rows():
+@pytest.mark.parametrize("precision", ["fp16_tc", "bf16_tc"])
+def test_tc_scalar_fallback_rows(precision):
     # thin, large splats far from their tiles' centres exercise the scalar FP32 rows of the
     # tensor-core path; the image still meets the tolerance
     scene = scenes.mixture_scene(3000, seed=41, components=4, cluster_std=0.2, radius=0.8,
                                  log_scale_mean=-2.5, log_scale_std=0.3, sh_degree=0,
                                  needle_fraction=0.5, needle_ratio=400.0)
     cam = scenes.orbit_cameras(4, 3.0, 256, 192)[1]
-    rgb, T, nc, img, _ = _raster_vs_oracle(scene, cam, (2, 2), "fp16_tc")
+    rgb, T, nc, img, _ = _raster_vs_oracle(scene, cam, (2, 2), precision)
     assert oracle.psnr(rgb, _chw(img.rgb)) >= TC_PSNR
     ok = img.margin > TC_MARGIN
     assert np.abs(rgb - _chw(img.rgb)).max(axis=0)[ok].max() <= TC_MAXABS
