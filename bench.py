@@ -173,6 +173,164 @@ def cpu_baseline(scene, cam, tc_image=None, target_s=12.0, seed=0):
 
 # ------------------------------------------------------------------------------------------------
 
+def _time_renderer(rend, ncams, steps, warmup):
+    """Mean frame ms of a Renderer over `steps` passes of its cameras (CUDA events)."""
+    import torch
+    for _ in range(warmup):
+        for i in range(ncams):
+            rend.render(i)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        for i in range(ncams):
+            rend.render(i)
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / (steps * ncams)
+
+
+def run_c3(args):
+    """6M Gaussians (64 tight clusters, 5% needles, SH degree 3) from 4 cameras at 3840x2160: every
+    grouping (1x1, 2x2, 4x2, 2x4, 4x4) in FP16 and BF16 and the FP32 CUDA-core path, timed with the
+    whole frame (preprocess, bin sort, rasterize) in CUDA graphs; the fastest grouping per precision
+    is reported (the autotune), with a per-image error report of its camera-0 image against the
+    oracle on sampled tile groups."""
+    import torch
+    import paper_2605_17855_gb300 as tgs
+    from paper_2605_17855_gb300 import scenes
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    scene, cams = scenes.config_c3()
+    H, W = cams[0].height, cams[0].width
+    ds = tgs.DeviceScene.from_host(scene)
+    steps = max(2, min(args.steps, 10))
+    table = {}
+    for prec in ("fp16_tc", "bf16_tc"):
+        for tl in ((1, 1), (2, 2), (4, 2), (2, 4), (4, 4)):
+            rend = tgs.Renderer(ds, cams, tl, prec)
+            table[f"{prec}_{tl[0]}x{tl[1]}"] = round(_time_renderer(rend, len(cams), steps, 3), 4)
+            if rend.overflowed():
+                raise RuntimeError("bin capacity overflow")
+            del rend
+            torch.cuda.empty_cache()
+    rend = tgs.Renderer(ds, cams, (1, 1), "fp32")
+    table["fp32_1x1"] = round(_time_renderer(rend, len(cams), steps, 3), 4)
+    del rend
+    best = {p: min((v, k) for k, v in table.items() if k.startswith(p)) for p in ("fp16_tc", "bf16_tc")}
+    errors = {}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        pix, ref = _oracle_sample(scene, cams[0], target_s=args.cpu_sample_s)
+        for prec, (_, key) in best.items():
+            tl = tuple(int(v) for v in key.split("_")[-1].split("x"))
+            rgb, _, _, _, _ = tgs.render(ds, cams[0], tl, prec)
+            torch.cuda.synchronize()
+            got = rgb.cpu().numpy()[:, pix[:, 1], pix[:, 0]].T
+            errors[prec] = {"tiling": key.split("_")[-1], "pixels": int(len(pix)),
+                            "psnr_db": round(oracle.psnr(got, ref), 2),
+                            "max_abs": float(np.abs(got - ref).max())}
+    px = len(cams) * W * H
+    out = {"metric": "rasterize Mpx/s, grouping x precision autotune (6M Gaussians, 3840x2160)",
+           "value": round(W * H / (best["fp16_tc"][0] * 1e-3) / 1e6, 2), "unit": "Mpx/s", "n_gpus": ws,
+           "higher_is_better": True, "dtype": DTYPE["fp16_tc"], "data": "synthetic",
+           "config": {"workload": "6M Gaussians, 64 clusters (std 0.15), 5% needles 100:1, SH degree 3; "
+                                  "4 orbit cameras at 3840x2160", "steps": steps, "pixels_per_step": px},
+           "frame_ms": table,
+           "autotune": {p: {"tiling": k.split("_")[-1], "frame_ms": v} for p, (v, k) in best.items()},
+           "speedup_vs_fp32_core": round(table["fp32_1x1"] / best["fp16_tc"][0], 3),
+           "error_vs_oracle": errors}
+    if rank == 0:
+        print(json.dumps(out))
+    return 0
+
+
+def run_c4(args):
+    """Forward (FP32 rasterize with n_contrib) + backward of the blend for 500k Gaussians (the c1
+    generator) from 8 jittered cameras at 1024x1024, L = sum(image * G) with a fixed random G."""
+    import torch
+    import paper_2605_17855_gb300 as tgs
+    from paper_2605_17855_gb300 import scenes
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    scene, cams = scenes.config_c4()
+    ds = tgs.DeviceScene.from_host(scene)
+    frames = []
+    for cam in cams:
+        proj = tgs.preprocess(ds, cam)
+        bins = tgs.bin_sort(proj, cam.width, cam.height, (2, 2))
+        G = torch.randn((3, cam.height, cam.width), device="cuda")
+        frames.append((cam, proj, bins, G))
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step():
+        for cam, proj, bins, G in frames:
+            rgb, T, nc = tgs.rasterize(proj, bins, cam.width, cam.height, "fp32")
+            tgs.rasterize_backward(proj, bins, cam.width, cam.height, T, nc, G)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    steps = max(3, min(args.steps, 20))
+    a, b = ev(), ev()
+    a.record()
+    for _ in range(steps):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    # backward alone
+    cam, proj, bins, G = frames[0]
+    rgb, T, nc = tgs.rasterize(proj, bins, cam.width, cam.height, "fp32")
+    a.record()
+    for _ in range(steps):
+        tgs.rasterize_backward(proj, bins, cam.width, cam.height, T, nc, G)
+    b.record()
+    torch.cuda.synchronize()
+    bwd_ms = a.elapsed_time(b) / steps
+    px = sum(c.width * c.height for c in cams)
+    out = {"metric": "forward+backward Mpx/s (500k Gaussians, 8 cameras at 1024x1024)",
+           "value": round(px / (ms * 1e-3) / 1e6, 2), "unit": "Mpx/s", "n_gpus": ws, "higher_is_better": True,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "500k Gaussians (c1 generator, SH degree 0), 8 yaw-jittered cameras at "
+                                  "1024x1024, 2x2 groups", "steps": steps},
+           "ms_per_step": round(ms, 4), "backward_ms_per_frame": round(bwd_ms, 4)}
+    if rank == 0:
+        print(json.dumps(out))
+    return 0
+
+
+def _oracle_sample(scene, cam, target_s=10.0, seed=0):
+    """The oracle's colours of random 2x2 tile groups of a frame (grown until about target_s of
+    oracle blending): (pixels [P,2] as (x, y), rgb [P,3])."""
+    import oracle
+    pr = oracle.preprocess(scene, cam)
+    bins = oracle.bin_sort(pr.mean2d, pr.radius, pr.depth, cam.width, cam.height, 2, 2)
+    TX, TY, GX, GY = oracle.group_grid(cam.width, cam.height, 2, 2)
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(GX * GY)
+    pix_list, ref_list = [], []
+    k, spent, batch = 0, 0.0, 8
+    while k < len(order) and spent < target_s:
+        gs = order[k:k + batch]
+        k += len(gs)
+        pix = []
+        for g in gs:
+            gx, gy = g % GX, g // GX
+            xs = np.arange(gx * 32, min(gx * 32 + 32, cam.width))
+            ys = np.arange(gy * 32, min(gy * 32 + 32, cam.height))
+            X, Y = np.meshgrid(xs, ys)
+            pix.append(np.stack([X.ravel(), Y.ravel()], 1))
+        pix = np.concatenate(pix)
+        t = time.perf_counter()
+        ref = oracle.blend(cam.width, cam.height, pr.mean2d, pr.conic, pr.opacity, pr.rgb, bins, pixels=pix)
+        spent += time.perf_counter() - t
+        pix_list.append(pix)
+        ref_list.append(ref.rgb)
+        batch = min(batch * 2, 256)
+    return np.concatenate(pix_list), np.concatenate(ref_list)
+
+
 def run_serve(args):
     """The rendering service on four resident scenes (200k / 800k / 1.5M / 3M Gaussians, SH degree 3)
     under a 120 GB budget: open-loop Poisson arrivals at --rate for --seconds, each request a random
@@ -337,6 +495,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     ap.add_argument("--ref-sample-s", type=float, default=8.0)
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"],
+                    help="c2: the headline frame benchmark; c3: 6M Gaussians at 3840x2160, grouping "
+                         "and precision autotune with a per-image error report; c4: forward + "
+                         "backward, 500k Gaussians at 1024x1024")
     ap.add_argument("--serve", action="store_true",
                     help="benchmark the rendering service on four resident scenes instead")
     ap.add_argument("--rate", type=float, default=1000.0, help="--serve: offered requests per second")
@@ -345,6 +507,10 @@ def main():
     args.warmup = max(args.warmup, 3)
     if args.serve:
         return run_serve(args)
+    if args.workload == "c3" and args.impl != "reference":
+        return run_c3(args)
+    if args.workload == "c4" and args.impl != "reference":
+        return run_c4(args)
     if args.impl == "reference":
         return run_reference(args)
 
