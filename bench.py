@@ -111,6 +111,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The largest of every rank's value (the time of the slowest replica); the value itself
+    without a process group."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world_size: int, pixels_per_step_per_rank: int, ms_per_step: float) -> float:
+    """Mpx/s of the whole job: every rank renders its own frames (weak scaling), the step time is
+    the slowest rank's."""
+    return world_size * pixels_per_step_per_rank / (ms_per_step * 1e-3) / 1e6
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -556,11 +573,8 @@ def main():
         torch.cuda.nvtx.range_pop()
         t1.record(stream)
         torch.cuda.synchronize()
-        total_ms = t0.elapsed_time(t1)
+        total_ms = max_over_ranks(t0.elapsed_time(t1), dist, "cuda")
         if dist:
-            tt = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            total_ms = float(tt.item())
             dist.barrier()
         frames = np.array([a.elapsed_time(c) for row in evs for a, _, c in row])
         prep = np.array([a.elapsed_time(m) for row in evs for a, m, _ in row])
@@ -574,14 +588,14 @@ def main():
     launches = int(args.steps * sum(rend.kernels_per_frame))
     ms_per_step = total_ms / args.steps
     px_per_step = len(cams) * W * H
-    value = ws * px_per_step / (ms_per_step * 1e-3) / 1e6
+    value = whole_job_rate(ws, px_per_step, ms_per_step)
     steps32 = max(3, args.steps // 2)
     tot32, frames32, prep32, raster32 = timed(rend32, steps32, 3)
-    value32 = ws * px_per_step / (tot32 / steps32 * 1e-3) / 1e6
+    value32 = whole_job_rate(ws, px_per_step, tot32 / steps32)
     ablation = None
     if rend_nc is not None:
         totnc, framesnc, _, rasternc = timed(rend_nc, steps32, 3)
-        ablation = {"value": round(ws * px_per_step / (totnc / steps32 * 1e-3) / 1e6, 3), "unit": UNIT,
+        ablation = {"value": round(whole_job_rate(ws, px_per_step, totnc / steps32), 3), "unit": UNIT,
                     "rasterize_ms_mean": round(float(rasternc.mean()), 4),
                     "note": "fp16_tc without the exact per-(Gaussian, tile) skip (identical images)"}
     # the other grouping / precision combinations of the comparison, each timed the same way
@@ -594,7 +608,7 @@ def main():
         if rv.overflowed():
             raise RuntimeError("bin capacity overflow during the benchmark")
         variants[f"{prec}_{tl[0]}x{tl[1]}"] = {
-            "value": round(ws * px_per_step / (totv / steps32 * 1e-3) / 1e6, 3), "unit": UNIT,
+            "value": round(whole_job_rate(ws, px_per_step, totv / steps32), 3), "unit": UNIT,
             "rasterize_ms_mean": round(float(rasterv.mean()), 4),
             "frame_ms_p99": round(float(np.percentile(framesv, 99)), 4)}
         del rv
@@ -658,12 +672,8 @@ def main():
         e2e_step()
     b.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = a.elapsed_time(b) / e2e_steps
-    if dist:
-        tt = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
-    e2e_value = ws * px_per_step / (e2e_ms * 1e-3) / 1e6
+    e2e_ms = max_over_ranks(a.elapsed_time(b) / e2e_steps, dist, "cuda")
+    e2e_value = whole_job_rate(ws, px_per_step, e2e_ms)
 
     peaks, peak_kind = _peaks()
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", SM_MAX_MHZ)

@@ -67,10 +67,10 @@ static tgs_status require_sm103(int32_t device) {
 static tgs_status require_current_sm103() {
   int dev = 0;
   TGS_CUDA(cudaGetDevice(&dev));
-  static int cached[64] = {0};  // 0 unknown, 1 ok, 2 unsupported
-  if (dev >= 0 && dev < 64 && cached[dev] == 1) return TGS_OK;
+  static std::atomic<int> cached[64];  // 0 unknown, 1 ok, 2 unsupported (zero-initialized)
+  if (dev >= 0 && dev < 64 && cached[dev].load(std::memory_order_relaxed) == 1) return TGS_OK;
   tgs_status s = require_sm103(dev);
-  if (dev >= 0 && dev < 64) cached[dev] = (s == TGS_OK) ? 1 : 2;
+  if (dev >= 0 && dev < 64) cached[dev].store((s == TGS_OK) ? 1 : 2, std::memory_order_relaxed);
   return s;
 }
 
