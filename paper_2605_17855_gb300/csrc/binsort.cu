@@ -29,6 +29,9 @@ constexpr int kSortThreads = 256;  // 8 warps
 constexpr int kSortItems = 16;     // per thread
 constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 items per tile
 constexpr int kMaxPasses = 4;
+// items per thread of the radix passes (tiles of 256 x items)
+constexpr int kDepthItems = 16;
+constexpr int kGidItems = 16;
 // Look-back status words: 2 flag bits over a 30-bit count (sizes are limited to < 2^30).
 constexpr uint32_t kFlagAgg = 1u << 30;     // the tile's own count is published
 constexpr uint32_t kFlagPrefix = 2u << 30;  // the inclusive prefix up to the tile is published
@@ -192,11 +195,13 @@ __device__ __forceinline__ void entry_outputs(const Finalize& f, uint32_t pos, u
 // ---------------------------------------------------------------------------------------------
 // One stable LSD radix pass (8-bit digit at `shift`) of (u32 key, u32 value) pairs, single kernel.
 // `ghist` holds the digit's counts over all items (from a histogram kernel run before the passes).
-// Each tile: each warp ranks its 512 consecutive items by digit (match_any); warps are ordered, so
+// Each tile of 256 * ITEMS items: each warp ranks its 32 * ITEMS consecutive items by digit
+// (match_any); warps are ordered, so
 // the tile's items get their stable rank in digit order. The tile's offset per digit is the
 // global start of the digit plus the counts of that digit in the earlier tiles (look-back). Items
 // are staged in shared memory in digit order and written so that each digit's run is contiguous
 // and consecutive threads store consecutive words.
+template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const int64_t* count_dev,
@@ -207,25 +212,32 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
   __shared__ uint32_t dstart[kRadix];     // tile-local start of each digit's run
   __shared__ uint32_t boff[kRadix];       // global start of this tile's run of each digit
   __shared__ uint32_t tmp[W];
-  __shared__ uint32_t skey[kSortTile], sval[kSortTile];
+  __shared__ uint32_t skey[kSortThreads * ITEMS], sval[kSortThreads * ITEMS];
   __shared__ int s_tile;
   if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1);
   for (int k = threadIdx.x; k < W * kRadix; k += kSortThreads) (&wcount[0][0])[k] = 0;
   __syncthreads();
   const int tile = s_tile;
   const int64_t count = live_count(count_dev, count_host, cap);
-  const int64_t block_base = (int64_t)tile * kSortTile;
+  const int64_t block_base = (int64_t)tile * (kSortThreads * ITEMS);
   if (block_base >= count) return;  // uniform per block; later tickets are past the end too
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
-  int dig[kSortItems];
+  uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
+  int dig[ITEMS];
+  // all loads first, so that they are in flight together (the ranking below synchronizes the warp
+  // between items)
 #pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
-    const int64_t i = block_base + (int64_t)warp * (32 * kSortItems) + r * 32 + lane;
+  for (int r = 0; r < ITEMS; ++r) {
+    const int64_t i = block_base + (int64_t)warp * (32 * ITEMS) + r * 32 + lane;
     const bool valid = i < count;
     key[r] = valid ? keys_in[i] : 0u;
     val[r] = valid ? vals_in[i] : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < ITEMS; ++r) {
+    const int64_t i = block_base + (int64_t)warp * (32 * ITEMS) + r * 32 + lane;
+    const bool valid = i < count;
     const int d = valid ? (int)((key[r] >> shift) & (kRadix - 1)) : kRadix;
     dig[r] = d;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
@@ -255,7 +267,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
   boff[d] = gstart + excl_tiles;
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
+  for (int r = 0; r < ITEMS; ++r) {
     const int dd = dig[r];
     if (dd < kRadix) {
       const uint32_t p = dstart[dd] + wcount[warp][dd] + rank[r];
@@ -264,7 +276,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     }
   }
   __syncthreads();
-  const int nvalid = (int)min((int64_t)kSortTile, count - block_base);
+  const int nvalid = (int)min((int64_t)(kSortThreads * ITEMS), count - block_base);
   for (int i = threadIdx.x; i < nvalid; i += kSortThreads) {
     const uint32_t k = skey[i];
     const int dd = (int)((k >> shift) & (kRadix - 1));
@@ -301,17 +313,27 @@ __global__ void __launch_bounds__(kSortThreads) k_depth_keys(
   const uint32_t lt_mask = (1u << lane) - 1u;
   uint32_t* hw = h[warp];
   uint32_t key[kSortItems], ball[kSortItems];
+  int rad[kSortItems];
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {  // item r of thread t: base + r * 256 + t
     const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
-    bool vis = false;
-    key[r] = 0u;
-    if (i < n && radius[i] > 0) {
-      vis = true;
-      // depth > near_z > 0, so the IEEE bits of a visible depth are monotone in the depth
-      key[r] = __float_as_uint(depth[i]);
+    rad[r] = i < n ? radius[i] : 0;
+    // depth > near_z > 0, so the IEEE bits of a visible depth are monotone in the depth
+    key[r] = i < n ? __float_as_uint(depth[i]) : 0u;
+  }
 #pragma unroll
-      for (int p = 0; p < 4; ++p) atomicAdd(&hw[p * kRadix + ((key[r] >> (8 * p)) & 0xffu)], 1u);
+  for (int r = 0; r < kSortItems; ++r) {
+    const bool vis = rad[r] > 0;
+    if (vis) {  // the two low digits are spread: plain shared atomics
+      atomicAdd(&hw[(key[r] & 0xffu)], 1u);
+      atomicAdd(&hw[kRadix + ((key[r] >> 8) & 0xffu)], 1u);
+    }
+    // the two high digits take few values over a frame: one atomic per distinct digit of the warp
+#pragma unroll
+    for (int p = 2; p < 4; ++p) {
+      const int d = vis ? (int)((key[r] >> (8 * p)) & 0xffu) : -1;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      if (vis && (__ffs(peers) - 1) == lane) atomicAdd(&hw[p * kRadix + d], __popc(peers));
     }
     ball[r] = __ballot_sync(0xffffffffu, vis);
     if (lane == 0) cnt[r][warp] = __popc(ball[r]);
@@ -387,22 +409,29 @@ __global__ void __launch_bounds__(kSortThreads) k_group_offsets(
   if ((int64_t)tile * kSortTile >= n) return;
   int32_t* D = dslices ? sD : dglobal;
   uint32_t c[kSortItems];
+  int4 rc[kSortItems];
   uint64_t sum = 0;
+  // loads first (the Gaussians in depth order are visible: compacted before the depth sort), so
+  // that the gathers of all items are in flight together
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
     const int64_t s = base + k;
+    c[k] = s < n ? order[s] : 0xFFFFFFFFu;
+  }
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k)
+    rc[k] = c[k] != 0xFFFFFFFFu ? rect[c[k]] : make_int4(0, 0, 0, 0);
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
     uint32_t v = 0;
-    if (s < n) {
-      const uint32_t i = order[s];
-      if (radius[i] > 0) {
-        const int4 r = rect[i];
-        const int gx0 = r.x / gw, gx1 = (r.z - 1) / gw + 1, gy0 = r.y / gh, gy1 = (r.w - 1) / gh + 1;
-        v = (uint32_t)((gx1 - gx0) * (gy1 - gy0));
-        atomicAdd(&D[gy0 * GXp1 + gx0], 1);
-        atomicAdd(&D[gy0 * GXp1 + gx1], -1);
-        atomicAdd(&D[gy1 * GXp1 + gx0], -1);
-        atomicAdd(&D[gy1 * GXp1 + gx1], 1);
-      }
+    const int4 r = rc[k];
+    if (r.z > r.x) {
+      const int gx0 = r.x / gw, gx1 = (r.z - 1) / gw + 1, gy0 = r.y / gh, gy1 = (r.w - 1) / gh + 1;
+      v = (uint32_t)((gx1 - gx0) * (gy1 - gy0));
+      atomicAdd(&D[gy0 * GXp1 + gx0], 1);
+      atomicAdd(&D[gy0 * GXp1 + gx1], -1);
+      atomicAdd(&D[gy1 * GXp1 + gx0], -1);
+      atomicAdd(&D[gy1 * GXp1 + gx1], 1);
     }
     c[k] = v;
     sum += v;
@@ -552,8 +581,12 @@ __global__ void __launch_bounds__(256) k_emit(const int64_t* __restrict__ visibl
       const int sw = __shfl_sync(0xffffffffu, gwn, lo);
       if (k < warp_total) {
         const int li = (int)(k - src_excl);
+        // li / sw exactly: (li + 1/2) / sw is at least 1/(2 sw) away from an integer, far more
+        // than the float rounding of the quotient (li < 2^24, sw <= 4096)
+        const int qy = (int)(((float)li + 0.5f) * __frcp_rn((float)sw));
+        const int qx = li - qy * sw;
         const uint64_t o = base + k;
-        gkeys[o] = (uint32_t)((sy + li / sw) * GX + (sx + li % sw));
+        gkeys[o] = (uint32_t)((sy + qy) * GX + (sx + qx));
         vals[o] = src_i;
       }
     }
@@ -579,7 +612,7 @@ struct WsLayout {
   size_t dkA, dkB, dvA, dvB, offs, gkA, gkB, gvB, dslices;
   size_t zero_begin, hist_d, hist_g, stat_d, stat_g, stat_o, stat_c, tickets, dsum, visible,
       zero_end;
-  int nb_d, nb_g, nb_o, cells;
+  int nb_c, nb_d, nb_g, nb_o, cells;
   bool sliced;  // the difference array fits in shared memory: per-tile slices
   size_t total;
 };
@@ -601,9 +634,10 @@ WsLayout layout(int64_t n, int64_t cap, int GX, int GY) {
     off += align256(bytes);
     return o;
   };
-  L.nb_d = (int)std::max<int64_t>(1, div_up(n, kSortTile));
-  L.nb_g = (int)std::max<int64_t>(1, div_up(cap, kSortTile));
-  L.nb_o = L.nb_d;
+  L.nb_c = (int)std::max<int64_t>(1, div_up(n, kSortTile));
+  L.nb_d = (int)std::max<int64_t>(1, div_up(n, kSortThreads * kDepthItems));
+  L.nb_g = (int)std::max<int64_t>(1, div_up(cap, kSortThreads * kGidItems));
+  L.nb_o = L.nb_c;
   const int gpasses = std::max(1, div_up(group_bits(G), kRadixBits));
   L.dkA = take(4 * (size_t)n);
   L.dkB = take(4 * (size_t)n);
@@ -622,7 +656,7 @@ WsLayout layout(int64_t n, int64_t cap, int GX, int GY) {
   L.stat_d = take(4 * (size_t)4 * L.nb_d * kRadix);
   L.stat_g = take(4 * (size_t)gpasses * L.nb_g * kRadix);
   L.stat_o = take(8 * (size_t)L.nb_o);
-  L.stat_c = take(8 * (size_t)L.nb_d);
+  L.stat_c = take(8 * (size_t)L.nb_c);
   L.tickets = take(4 * (4 + kMaxPasses + 2));
   L.visible = take(8);
   L.dsum = take(4 * (size_t)L.cells);
@@ -677,13 +711,13 @@ tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int h
   //    single-kernel radix passes over the visible count
   auto* visible = reinterpret_cast<int64_t*>(w + L.visible);
   auto* stat_c = reinterpret_cast<uint64_t*>(w + L.stat_c);
-  k_depth_keys<<<L.nb_d, kSortThreads, 0, st>>>(n, p.radius, p.depth, dkA, dvA, visible, hist_d,
+  k_depth_keys<<<L.nb_c, kSortThreads, 0, st>>>(n, p.radius, p.depth, dkA, dvA, visible, hist_d,
                                                 stat_c, tickets + 4 + kMaxPasses + 1, err);
   TGS_CHECK_LAUNCH("k_depth_keys");
   const Finalize fin{rect, p.depth, gw, gh, GX, b.masks, b.keys};
   for (int pass = 0; pass < 4; ++pass) {
     const bool odd = pass & 1;
-    k_onesweep<<<L.nb_d, kSortThreads, 0, st>>>(
+    k_onesweep<kDepthItems><<<L.nb_d, kSortThreads, 0, st>>>(
         odd ? dkB : dkA, odd ? dvB : dvA, odd ? dkA : dkB, odd ? dvA : dvB, visible, 0, n,
         8 * pass, hist_d + pass * kRadix, stat_d + (size_t)pass * L.nb_d * kRadix, tickets + pass,
         err);
@@ -726,7 +760,7 @@ tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int h
   const uint32_t* gk = ek;
   for (int pass = 0; pass < passes; ++pass) {
     const bool odd = pass & 1;
-    k_onesweep<<<L.nb_g, kSortThreads, 0, st>>>(
+    k_onesweep<kGidItems><<<L.nb_g, kSortThreads, 0, st>>>(
         odd ? ok : ek, odd ? ov : ev, odd ? ek : ok, odd ? ev : ov, b.num_entries, 0, cap,
         8 * pass, hist_g + pass * kRadix, stat_g + (size_t)pass * L.nb_g * kRadix, tickets + 4 + pass,
         err);
