@@ -202,6 +202,7 @@ def _time_renderer(rend, ncams, steps, warmup):
     for _ in range(steps):
         for i in range(ncams):
             rend.render(i)
+    rend.join()
     b.record()
     torch.cuda.synchronize()
     return a.elapsed_time(b) / (steps * ncams)
@@ -551,6 +552,10 @@ def main():
     # one pair of CUDA graphs per camera (preprocess + bin sort, rasterize): a frame is two launches
     rend = tgs.Renderer(ds, cams, tiling, args.precision)
     rend32 = tgs.Renderer(ds, cams, (1, 1), "fp32")  # the plain tile rasterizer, 1x1 tiles
+    # the same frames without the two-stream pipeline: the per-stage split and the rasterize
+    # kernel's own launch time (for the roofline) come from these
+    rend_serial = tgs.Renderer(ds, cams, tiling, args.precision, pipeline=False)
+    rend32_serial = tgs.Renderer(ds, cams, (1, 1), "fp32", pipeline=False)
     # ablation: the same tensor-core path without the exact (Gaussian, tile) skip
     rend_nc = tgs.Renderer(ds, cams, tiling, args.precision, cull=False) if args.precision != "fp32" else None
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
@@ -570,13 +575,19 @@ def main():
         for k in range(steps):
             for i in range(len(cams)):
                 r.render(i, evs[k][i])
+        r.join()
         torch.cuda.nvtx.range_pop()
         t1.record(stream)
         torch.cuda.synchronize()
         total_ms = max_over_ranks(t0.elapsed_time(t1), dist, "cuda")
         if dist:
             dist.barrier()
-        frames = np.array([a.elapsed_time(c) for row in evs for a, _, c in row])
+        # frame time = interval between consecutive frame completions (what a viewer of the
+        # frame sequence sees); latency = from a frame's first kernel to its last
+        ends = [c for row in evs for _, _, c in row]
+        frames = np.array([t0.elapsed_time(ends[0])] +
+                          [ends[q - 1].elapsed_time(ends[q]) for q in range(1, len(ends))])
+        timed.latency = np.array([a.elapsed_time(c) for row in evs for a, _, c in row])
         prep = np.array([a.elapsed_time(m) for row in evs for a, m, _ in row])
         raster = np.array([m.elapsed_time(c) for row in evs for _, m, c in row])
         return total_ms, frames, prep, raster
@@ -584,19 +595,22 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     total_ms, frames_ms, prep_ms, raster_ms = timed(rend, args.steps, args.warmup)
+    latency_ms = timed.latency
     clocks = sampler.stop()
     launches = int(args.steps * sum(rend.kernels_per_frame))
     ms_per_step = total_ms / args.steps
     px_per_step = len(cams) * W * H
     value = whole_job_rate(ws, px_per_step, ms_per_step)
     steps32 = max(3, args.steps // 2)
-    tot32, frames32, prep32, raster32 = timed(rend32, steps32, 3)
+    tot32, frames32, _, _ = timed(rend32, steps32, 3)
     value32 = whole_job_rate(ws, px_per_step, tot32 / steps32)
+    # without the pipeline: the stage split and the kernels' own rasterize times
+    tots, _, prep_ms, raster_ms = timed(rend_serial, steps32, 3)
+    tot32s, _, prep32, raster32 = timed(rend32_serial, steps32, 3)
     ablation = None
     if rend_nc is not None:
-        totnc, framesnc, _, rasternc = timed(rend_nc, steps32, 3)
+        totnc, framesnc, _, _ = timed(rend_nc, steps32, 3)
         ablation = {"value": round(whole_job_rate(ws, px_per_step, totnc / steps32), 3), "unit": UNIT,
-                    "rasterize_ms_mean": round(float(rasternc.mean()), 4),
                     "note": "fp16_tc without the exact per-(Gaussian, tile) skip (identical images)"}
     # the other grouping / precision combinations of the comparison, each timed the same way
     variants = {}
@@ -604,26 +618,27 @@ def main():
         if (prec, tl) == (args.precision, tiling):
             continue
         rv = tgs.Renderer(ds, cams, tl, prec)
-        totv, framesv, _, rasterv = timed(rv, steps32, 3)
+        totv, framesv, _, _ = timed(rv, steps32, 3)
         if rv.overflowed():
             raise RuntimeError("bin capacity overflow during the benchmark")
         variants[f"{prec}_{tl[0]}x{tl[1]}"] = {
             "value": round(whole_job_rate(ws, px_per_step, totv / steps32), 3), "unit": UNIT,
-            "rasterize_ms_mean": round(float(rasterv.mean()), 4),
             "frame_ms_p99": round(float(np.percentile(framesv, 99)), 4)}
         del rv
-    if rend.overflowed() or rend32.overflowed():
+    if rend.overflowed() or rend32.overflowed() or rend_serial.overflowed() or rend32_serial.overflowed():
         raise RuntimeError("bin capacity overflow during the benchmark")
 
     # split of the preprocess + bin sort stage for one frame (direct calls, untimed by the main loop)
     e = [ev() for _ in range(3)]
     e[0].record(stream)
-    tgs.preprocess(ds, cams[0], out=rend.proj)
+    tgs.preprocess(ds, cams[0], out=rend_serial.proj)
     e[1].record(stream)
-    tgs.bin_sort(rend.proj, W, H, tiling, bins=rend.bins, sync=False)
+    tgs.bin_sort(rend_serial.proj, W, H, tiling, bins=rend_serial.bins, sync=False)
     e[2].record(stream)
     torch.cuda.synchronize()
-    stages = {"preprocess_plus_bin_sort_ms": round(float(prep_ms.mean()), 4),
+    stages = {"note": "frames without the two-stream pipeline (CUDA events between the stages)",
+              "value_without_pipeline": round(whole_job_rate(ws, px_per_step, tots / steps32), 3),
+              "preprocess_plus_bin_sort_ms": round(float(prep_ms.mean()), 4),
               "rasterize_ms": round(float(raster_ms.mean()), 4),
               "preprocess_ms_direct": round(e[0].elapsed_time(e[1]), 4),
               "bin_sort_ms_direct": round(e[1].elapsed_time(e[2]), 4)}
@@ -635,12 +650,13 @@ def main():
     cnt_skip = torch.zeros(3, dtype=torch.int64, device="cuda")
     entries = 0
     for i, cam in enumerate(cams):
-        tgs.preprocess(ds, cam, out=rend.proj)
-        tgs.bin_sort(rend.proj, W, H, tiling, bins=rend.bins, sync=False)
+        tgs.preprocess(ds, cam, out=rend_serial.proj)
+        tgs.bin_sort(rend_serial.proj, W, H, tiling, bins=rend_serial.bins, sync=False)
         for c, cull in ((cnt, False), (cnt_skip, True)):
-            tgs.rasterize(rend.proj, rend.bins, W, H, args.precision, out=(rend.out[i][0], rend.out[i][1], None),
+            tgs.rasterize(rend_serial.proj, rend_serial.bins, W, H, args.precision,
+                          out=(rend_serial.out[i][0], rend_serial.out[i][1], None),
                           want_n_contrib=False, counters=c, cull=cull)
-        entries += int(rend.bins.num_entries.item())
+        entries += int(rend_serial.bins.num_entries.item())
     torch.cuda.synchronize()
     pairs, exps, _ = [int(v) / len(cams) for v in cnt.cpu().tolist()]
     pairs_after_skip = int(cnt_skip[0].item()) / len(cams)
@@ -659,8 +675,10 @@ def main():
         for k, t in host.items():
             getattr(ds, k).copy_(t, non_blocking=True)
         for i in range(len(cams)):
-            rgb, _ = rend.render(i)
-            host_imgs[i].copy_(rgb, non_blocking=True)
+            rend.render(i)
+        rend.join()
+        for i in range(len(cams)):
+            host_imgs[i].copy_(rend.out[i][0], non_blocking=True)
 
     for _ in range(2):
         e2e_step()
@@ -702,10 +720,16 @@ def main():
            "dtype": DTYPE[args.precision],
            "data": "synthetic", "config": _config(scene, cams, args),
            "frame_ms": {"mean": round(float(frames_ms.mean()), 4), "p50": round(float(np.percentile(frames_ms, 50)), 4),
-                        "p99": round(float(np.percentile(frames_ms, 99)), 4)},
+                        "p99": round(float(np.percentile(frames_ms, 99)), 4),
+                        "definition": "interval between consecutive frame completions"},
+           "frame_latency_ms": {"p50": round(float(np.percentile(latency_ms, 50)), 4),
+                                "p99": round(float(np.percentile(latency_ms, 99)), 4),
+                                "definition": "first kernel of the frame to its last (includes waiting for "
+                                              "the previous frame's rasterize)"},
            "fps": round(1000.0 / float(frames_ms.mean()), 2),
            "fp32_core_1x1": {"value": round(value32, 3), "unit": UNIT,
                              "frame_ms_p99": round(float(np.percentile(frames32, 99)), 4),
+                             "value_without_pipeline": round(whole_job_rate(ws, px_per_step, tot32s / steps32), 3),
                              "preprocess_plus_bin_sort_ms": round(float(prep32.mean()), 4),
                              "rasterize_ms_mean": round(float(raster32.mean()), 4)},
            "fp16_tc_without_tile_skip": ablation,
@@ -718,7 +742,8 @@ def main():
                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4)},
            "gpu_launches": launches,
            "kernels_per_frame": rend.kernels_per_frame[0],
-           "graphs": "one CUDA graph pair per camera (preprocess + bin sort, rasterize)",
+           "graphs": "one CUDA graph pair per camera (preprocess + bin sort, rasterize); the preprocess + "
+                     "bin sort of a frame runs on a second stream, overlapping the previous frame's rasterize",
            "clocks": clocks,
            "roofline": roofline}
 
@@ -726,6 +751,7 @@ def main():
         for k, t in host.items():  # restore the scene (the e2e loop copied the same values back)
             getattr(ds, k).copy_(t)
         rgb, _ = rend.render(0)
+        rend.join()
         torch.cuda.synchronize()
         rec, psnr = cpu_baseline(scene, cams[0], tc_image=rgb.cpu().numpy(), target_s=args.cpu_sample_s)
         out["cpu_baseline"] = rec

@@ -443,27 +443,42 @@ class Renderer:
     cached between frames. Capacities are sized once from a synchronous count per camera
     (x `margin`); a frame that outgrows its capacity renders background only and reports it through
     `overflowed()`.
+
+    With `pipeline` (default) the preprocess + bin sort of a frame runs on a second stream with its
+    own buffer set (two sets, alternating by camera index), so it overlaps the rasterization of the
+    previous frame; each set is reused only after the rasterization that read it. Frames are enqueued
+    by render(); join() makes the current stream wait for every enqueued frame. Images are the same
+    as without the pipeline.
     """
 
     def __init__(self, scene: DeviceScene, cameras, tiling=(2, 2), precision="fp16_tc",
-                 bg=(0.0, 0.0, 0.0), margin=1.1, graphs=True, cull=True):
+                 bg=(0.0, 0.0, 0.0), margin=1.1, graphs=True, cull=True, pipeline=True):
         self.cull = cull
         self.scene, self.cameras = scene, list(cameras)
         self.tiling, self.precision, self.bg = tuple(tiling), precision, tuple(bg)
+        self.pipeline = bool(pipeline)
         n = scene.n
-        self.proj = Projected.empty(n, scene.means.device)
+        dev = scene.means.device
+        nsets = 2 if self.pipeline else 1
+        self.proj_sets = [Projected.empty(n, dev) for _ in range(nsets)]
+        self.proj = self.proj_sets[0]
         cap = 0
         for cam in self.cameras:
             preprocess(scene, cam, out=self.proj)
             cap = max(cap, bin_sort(self.proj, cam.width, cam.height, self.tiling).entries)
         W = max(c.width for c in self.cameras)
         H = max(c.height for c in self.cameras)
-        # bin buffers are shared by all cameras (ranges sized for the largest image)
-        self.bins = allocate_bins(n, int(cap * margin) + 4096, W, H, self.tiling, keys=False)
-        self.out = [(torch.empty((3, c.height, c.width), device=scene.means.device),
-                     torch.empty((c.height, c.width), device=scene.means.device)) for c in self.cameras]
+        # bin buffers are shared by the cameras of a set (ranges sized for the largest image)
+        self.bin_sets = [allocate_bins(n, int(cap * margin) + 4096, W, H, self.tiling, keys=False)
+                         for _ in range(nsets)]
+        self.bins = self.bin_sets[0]
+        self.out = [(torch.empty((3, c.height, c.width), device=dev),
+                     torch.empty((c.height, c.width), device=dev)) for c in self.cameras]
         self.kernels_per_frame = []
         self.g_prep, self.g_raster = [], []
+        self.s_prep = torch.cuda.Stream(device=dev) if self.pipeline else None
+        self.s_raster = torch.cuda.Stream(device=dev) if self.pipeline else None
+        self._set_free = [None] * nsets  # event after the last rasterization that read each set
         for k in range(len(self.cameras)):  # run every path once outside capture
             self._prep(k)
             self._raster(k)
@@ -482,35 +497,73 @@ class Renderer:
                 self.g_raster.append(gr)
             torch.cuda.synchronize()
 
+    def _set(self, k):
+        return k % len(self.proj_sets)
+
     def _prep(self, k):
         cam = self.cameras[k]
-        preprocess(self.scene, cam, out=self.proj)
-        bin_sort(self.proj, cam.width, cam.height, self.tiling, bins=self.bins, sync=False)
+        proj, bins = self.proj_sets[self._set(k)], self.bin_sets[self._set(k)]
+        preprocess(self.scene, cam, out=proj)
+        bin_sort(proj, cam.width, cam.height, self.tiling, bins=bins, sync=False)
 
     def _raster(self, k):
         cam = self.cameras[k]
+        proj, bins = self.proj_sets[self._set(k)], self.bin_sets[self._set(k)]
         rgb, T = self.out[k]
-        rasterize(self.proj, self.bins, cam.width, cam.height, self.precision, self.bg, out=(rgb, T, None),
+        rasterize(proj, bins, cam.width, cam.height, self.precision, self.bg, out=(rgb, T, None),
                   want_n_contrib=False, cull=self.cull)
 
     def render(self, k, events=None):
-        """Renders camera k on the current stream; returns (rgb [3,H,W], T [H,W]) (reused buffers).
-        `events`, if given, are three CUDA events recorded before, between and after the two
-        stages."""
-        stream = torch.cuda.current_stream()
-        if events:
-            events[0].record(stream)
-        self.g_prep[k].replay() if self.g_prep else self._prep(k)
-        if events:
-            events[1].record(stream)
-        self.g_raster[k].replay() if self.g_raster else self._raster(k)
-        if events:
-            events[2].record(stream)
+        """Enqueues the frame of camera k; returns (rgb [3,H,W], T [H,W]) (reused buffers, ready
+        after join()). `events`, if given, are three CUDA events recorded before the preprocess,
+        after the bin sort and after the rasterization."""
+        cur = torch.cuda.current_stream()
+        if not self.pipeline:
+            if events:
+                events[0].record(cur)
+            self.g_prep[k].replay() if self.g_prep else self._prep(k)
+            if events:
+                events[1].record(cur)
+            self.g_raster[k].replay() if self.g_raster else self._raster(k)
+            if events:
+                events[2].record(cur)
+            return self.out[k]
+        st = self._set(k)
+        ready = torch.cuda.Event()
+        ready.record(cur)  # the caller's work issued so far (e.g. a scene upload)
+        with torch.cuda.stream(self.s_prep):
+            self.s_prep.wait_event(ready)
+            if self._set_free[st] is not None:
+                self.s_prep.wait_event(self._set_free[st])
+            if events:
+                events[0].record(self.s_prep)
+            self.g_prep[k].replay() if self.g_prep else self._prep(k)
+            prepped = torch.cuda.Event()
+            prepped.record(self.s_prep)
+            if events:
+                events[1].record(self.s_prep)
+        with torch.cuda.stream(self.s_raster):
+            self.s_raster.wait_event(prepped)
+            self.g_raster[k].replay() if self.g_raster else self._raster(k)
+            done = torch.cuda.Event()
+            done.record(self.s_raster)
+            if events:
+                events[2].record(self.s_raster)
+        self._set_free[st] = done
         return self.out[k]
 
+    def join(self):
+        """Makes the current stream wait for every frame enqueued so far."""
+        if self.pipeline:
+            cur = torch.cuda.current_stream()
+            cur.wait_stream(self.s_raster)
+            cur.wait_stream(self.s_prep)
+
     def overflowed(self) -> bool:
-        """True if the last rendered frame needed more bin entries than the capacity (synchronizes)."""
-        return int(self.bins.num_entries.item()) > self.bins.capacity
+        """True if the last frame of a buffer set needed more bin entries than the capacity
+        (synchronizes)."""
+        torch.cuda.synchronize()
+        return any(int(b.num_entries.item()) > b.capacity for b in self.bin_sets)
 
 
 # ------------------------------------------------------------------------------------------------

@@ -404,3 +404,25 @@ def test_autograd_function():
     for a, b in ((m.grad, gm), (co.grad, gco), (c.grad, gc)):
         assert torch.allclose(a, b, rtol=1e-4, atol=1e-6 * float(b.abs().max()))
     assert math.isfinite(float(loss))
+
+
+@pytest.mark.parametrize("pipeline", [True, False])
+def test_renderer_frames_equal_direct_path(pipeline):
+    # the CUDA-graph renderer (with and without the two-stream pipeline and its alternating buffer
+    # sets) produces exactly the frames of the direct preprocess -> bin sort -> rasterize calls
+    scene = scenes.mixture_scene(40_000, seed=31, components=32, cluster_std=0.3, radius=2.0,
+                                 log_scale_mean=-3.8, sh_degree=3, needle_fraction=0.05)
+    cams = scenes.orbit_cameras(8, 5.0, 320, 240)[:5]
+    ds = tgs.DeviceScene.from_host(scene)
+    rend = tgs.Renderer(ds, cams, (2, 2), "fp16_tc", pipeline=pipeline)
+    for _ in range(2):
+        for i in range(len(cams)):
+            rend.render(i)
+    rend.join()
+    torch.cuda.synchronize()
+    assert not rend.overflowed()
+    for i, cam in enumerate(cams):
+        rgb, T, _, _, _ = tgs.render(ds, cam, (2, 2), "fp16_tc")
+        torch.cuda.synchronize()
+        assert torch.equal(rend.out[i][0], rgb)
+        assert torch.equal(rend.out[i][1], T)
