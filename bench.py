@@ -208,7 +208,7 @@ def _time_renderer(rend, ncams, steps, warmup):
     return a.elapsed_time(b) / (steps * ncams)
 
 
-def run_c3(args):
+def run_dense4k(args):
     """6M Gaussians (64 tight clusters, 5% needles, SH degree 3) from 4 cameras at 3840x2160: every
     grouping (1x1, 2x2, 4x2, 2x4, 4x4) in FP16 and BF16 and the FP32 CUDA-core path, timed with the
     whole frame (preprocess, bin sort, rasterize) in CUDA graphs; the fastest grouping per precision
@@ -219,7 +219,7 @@ def run_c3(args):
     from paper_2605_17855_gb300 import scenes
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
-    scene, cams = scenes.config_c3()
+    scene, cams = scenes.clusters_6m_3840x2160()
     H, W = cams[0].height, cams[0].width
     ds = tgs.DeviceScene.from_host(scene)
     steps = max(2, min(args.steps, 10))
@@ -263,15 +263,15 @@ def run_c3(args):
     return 0
 
 
-def run_c4(args):
-    """Forward (FP32 rasterize with n_contrib) + backward of the blend for 500k Gaussians (the c1
+def run_backward(args):
+    """Forward (FP32 rasterize with n_contrib) + backward of the blend for 500k Gaussians (the box
     generator) from 8 jittered cameras at 1024x1024, L = sum(image * G) with a fixed random G."""
     import torch
     import paper_2605_17855_gb300 as tgs
     from paper_2605_17855_gb300 import scenes
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
-    scene, cams = scenes.config_c4()
+    scene, cams = scenes.box_500k_1024_8cams()
     ds = tgs.DeviceScene.from_host(scene)
     frames = []
     for cam in cams:
@@ -310,7 +310,7 @@ def run_c4(args):
     out = {"metric": "forward+backward Mpx/s (500k Gaussians, 8 cameras at 1024x1024)",
            "value": round(px / (ms * 1e-3) / 1e6, 2), "unit": "Mpx/s", "n_gpus": ws, "higher_is_better": True,
            "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "500k Gaussians (c1 generator, SH degree 0), 8 yaw-jittered cameras at "
+           "config": {"workload": "500k Gaussians (box generator, SH degree 0), 8 yaw-jittered cameras at "
                                   "1024x1024, 2x2 groups", "steps": steps},
            "ms_per_step": round(ms, 4), "backward_ms_per_frame": round(bwd_ms, 4)}
     if rank == 0:
@@ -360,8 +360,8 @@ def run_serve(args):
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     tiling = tuple(int(v) for v in args.tiling.split("x"))
-    sc = scenes.config_c5_scenes()
-    cams = [scenes.identity_camera(w, h) for (w, h) in scenes.C5_RESOLUTIONS]
+    sc = scenes.resident_scenes_200k_800k_1p5m_3m()
+    cams = [scenes.identity_camera(w, h) for (w, h) in scenes.SERVING_RESOLUTIONS]
     max_inflight = 64
     srv = tgs.Server(120 << 30, max_inflight=max_inflight, slots=8, device=local, precision=args.precision,
                      tiling=tiling)
@@ -442,7 +442,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_2605_17855_gb300 import scenes
-    scene, cams = scenes.config_c2()
+    scene, cams = scenes.mixture_1p5m_1600x1064()
     cam = cams[0]
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up state
@@ -513,9 +513,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     ap.add_argument("--ref-sample-s", type=float, default=8.0)
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"],
-                    help="c2: the headline frame benchmark; c3: 6M Gaussians at 3840x2160, grouping "
-                         "and precision autotune with a per-image error report; c4: forward + "
+    ap.add_argument("--workload", default="frames", choices=["frames", "dense4k", "backward"],
+                    help="frames: the headline frame benchmark; dense4k: 6M Gaussians at 3840x2160, grouping "
+                         "and precision autotune with a per-image error report; backward: forward + "
                          "backward, 500k Gaussians at 1024x1024")
     ap.add_argument("--serve", action="store_true",
                     help="benchmark the rendering service on four resident scenes instead")
@@ -525,10 +525,10 @@ def main():
     args.warmup = max(args.warmup, 3)
     if args.serve:
         return run_serve(args)
-    if args.workload == "c3" and args.impl != "reference":
-        return run_c3(args)
-    if args.workload == "c4" and args.impl != "reference":
-        return run_c4(args)
+    if args.workload == "dense4k" and args.impl != "reference":
+        return run_dense4k(args)
+    if args.workload == "backward" and args.impl != "reference":
+        return run_backward(args)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -545,7 +545,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     tiling = tuple(int(v) for v in args.tiling.split("x"))
 
-    scene, cams = scenes.config_c2(n=args.splats)
+    scene, cams = scenes.mixture_1p5m_1600x1064(n=args.splats)
     H, W = cams[0].height, cams[0].width
     ds = tgs.DeviceScene.from_host(scene)
     stream = torch.cuda.current_stream()

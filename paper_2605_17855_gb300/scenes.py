@@ -6,13 +6,16 @@ determined by its seed.
 
 The workloads stand in for the captured scenes the paper evaluates on (Section 5.1, Table 4:
 Tanks&Temples, Deep Blending, Synthetic-NeRF, Synthetic-NSVF), whose trained Gaussian models are not
-available. Their shapes follow the five rasterizer configurations:
+available. The workloads:
 
-  c1  2,000 splats in a camera-space box, SH degree 0, 128x128, one camera          (seed 0)
-  c2  1.5M splats from a 256-component mixture, SH degree 3, 1600x1064, 8 orbit cams (seed 2)
-  c3  6M splats in 64 tight clusters with 5% needles, SH degree 3, 3840x2160         (seed 3)
-  c4  500k splats (c1 generator), 8 jittered cameras at 1024x1024                    (seed 4)
-  c5  four resident scenes of 200k/800k/1.5M/3M splats (c1 generator, SH degree 3)   (seed 5)
+  box_2k_128                  2,000 splats in a camera-space box, SH degree 0, 128x128, one camera (seed 0)
+  mixture_1p5m_1600x1064      1.5M splats from a 256-component mixture, SH degree 3, 1600x1064, 8 orbit
+                              cameras (seed 2)
+  clusters_6m_3840x2160       6M splats in 64 tight clusters with 5% needles, SH degree 3, 3840x2160
+                              (seed 3)
+  box_500k_1024_8cams         500k splats from the box generator, 8 jittered cameras at 1024x1024 (seed 4)
+  resident_scenes_200k_800k_1p5m_3m  four scenes of 200k/800k/1.5M/3M splats from the box generator,
+                              SH degree 3 (seeds 5..8)
 
 Conventions (shared by both sides):
   * quaternions are (w, x, y, z) and unit norm;
@@ -142,7 +145,7 @@ def _sh_from_colour(rng, colour, degree, rest_std=0.1):
 
 def box_scene(n: int, seed: int = 0, sh_degree: int = 0, log_scale_mean: float = -3.5,
               log_scale_std: float = 0.5, opacity_logit_std: float = 1.5) -> Scene:
-    """c1 generator: means uniform in [-1,1]^2 x [2,6] (camera-space box of the identity camera),
+    """Box generator: means uniform in [-1,1]^2 x [2,6] (camera-space box of the identity camera),
     log-scales ~ N(mean, std) per axis, uniform unit quaternions, opacity = sigmoid(N(0, 1.5)),
     base colour uniform in [0,1] (higher SH bands ~ N(0, 0.1) when sh_degree > 0)."""
     rng = np.random.default_rng(seed)
@@ -176,7 +179,7 @@ def mixture_scene(n: int, seed: int, components: int = 256, cluster_std: float =
                   radius: float = 4.0, log_scale_mean: float = -4.5, log_scale_std: float = 0.8,
                   opacity_logit_std: float = 2.0, sh_degree: int = 3,
                   needle_fraction: float = 0.0, needle_ratio: float = 100.0) -> Scene:
-    """c2/c3 generator: means from an equal-weight Gaussian mixture whose centres are uniform in the
+    """Mixture generator: means from an equal-weight Gaussian mixture whose centres are uniform in the
     ball of `radius` (samples redrawn until inside it); log-scales ~ N(mean, std) per axis; opacity =
     sigmoid(N(0, std)); SH DC ~ U[0,1] (raw coefficient), higher bands ~ N(0, 0.1). A
     `needle_fraction` of splats get scales (10 s, s/10, s/10), an axis ratio of `needle_ratio`."""
@@ -202,12 +205,12 @@ def mixture_scene(n: int, seed: int, components: int = 256, cluster_std: float =
 # ----------------------------------------------------------------------------------------------
 # The five workload configurations.
 
-def config_c1():
+def box_2k_128():
     """2,000 splats, seed 0, SH degree 0, 128x128, 60 deg horizontal FOV, identity camera."""
     return box_scene(2000, seed=0, sh_degree=0), [identity_camera(128, 128, 60.0)]
 
 
-def config_c2(n: int = 1_500_000, cams: int = 8, width: int = 1600, height: int = 1064):
+def mixture_1p5m_1600x1064(n: int = 1_500_000, cams: int = 8, width: int = 1600, height: int = 1064):
     """1.5M-splat mixture scene (256 clusters, std 0.3, radius 4), SH degree 3, eight orbit
     cameras at radius 5 rendering 1600x1064."""
     return (mixture_scene(n, seed=2, components=256, cluster_std=0.3, radius=4.0,
@@ -215,7 +218,7 @@ def config_c2(n: int = 1_500_000, cams: int = 8, width: int = 1600, height: int 
             orbit_cameras(cams, 5.0, width, height))
 
 
-def config_c3(n: int = 6_000_000, cams: int = 4, width: int = 3840, height: int = 2160):
+def clusters_6m_3840x2160(n: int = 6_000_000, cams: int = 4, width: int = 3840, height: int = 2160):
     """6M splats in 64 tight clusters (std 0.15) with 5% needles (axis ratio 100:1), SH degree 3,
     four orbit views at radius 5 rendering 3840x2160."""
     return (mixture_scene(n, seed=3, components=64, cluster_std=0.15, radius=4.0,
@@ -224,8 +227,8 @@ def config_c3(n: int = 6_000_000, cams: int = 4, width: int = 3840, height: int 
             orbit_cameras(cams, 5.0, width, height))
 
 
-def config_c4(n: int = 500_000, cams: int = 8, size: int = 1024):
-    """500k splats from the c1 generator; eight cameras yaw-jittered by up to +-10 degrees about the
+def box_500k_1024_8cams(n: int = 500_000, cams: int = 8, size: int = 1024):
+    """500k splats from the box generator; eight cameras yaw-jittered by up to +-10 degrees about the
     scene centre (0, 0, 4) at 1024x1024."""
     scene = box_scene(n, seed=4, sh_degree=0)
     rng = np.random.default_rng(1004)
@@ -238,9 +241,9 @@ def config_c4(n: int = 500_000, cams: int = 8, size: int = 1024):
     return scene, out
 
 
-def config_c5_scenes(sizes=(200_000, 800_000, 1_500_000, 3_000_000)):
-    """Four resident scenes from the c1 generator with SH degree 3."""
+def resident_scenes_200k_800k_1p5m_3m(sizes=(200_000, 800_000, 1_500_000, 3_000_000)):
+    """Four resident scenes from the box generator with SH degree 3."""
     return [box_scene(n, seed=5 + i, sh_degree=3) for i, n in enumerate(sizes)]
 
 
-C5_RESOLUTIONS = ((640, 480), (1280, 720), (1920, 1080), (2 * 2048, 2048))
+SERVING_RESOLUTIONS = ((640, 480), (1280, 720), (1920, 1080), (2 * 2048, 2048))

@@ -84,7 +84,7 @@ def _mixture_small():
 
 
 CASES = {
-    "c1": lambda: (lambda s, c: (s, c[0]))(*scenes.config_c1()),
+    "box2k": lambda: (lambda s, c: (s, c[0]))(*scenes.box_2k_128()),
     "ragged": _ragged,
     "mixture": _mixture_small,
 }
@@ -142,7 +142,7 @@ def test_bin_sort_bit_exact(case, tiling):
 
 
 def test_bin_sort_capacity_overflow():
-    scene, cams = scenes.config_c1()
+    scene, cams = scenes.box_2k_128()
     cam = cams[0]
     ds = tgs.DeviceScene.from_host(scene)
     proj = tgs.preprocess(ds, cam)
@@ -278,7 +278,7 @@ def test_background_and_empty_inputs():
 
 
 def test_background_blend():
-    scene, cams = scenes.config_c1()
+    scene, cams = scenes.box_2k_128()
     cam = cams[0]
     bg = (0.2, 0.4, 0.6)
     _, proj, bins = _gpu_frame(scene, cam)
@@ -312,7 +312,7 @@ def test_tc_scalar_fallback_rows(precision):
 
 @pytest.fixture(scope="module")
 def c2_frame():
-    scene, cams = scenes.config_c2()
+    scene, cams = scenes.mixture_1p5m_1600x1064()
     cam = cams[0]
     ds, proj, bins = _gpu_frame(scene, cam, (2, 2))
     torch.cuda.synchronize()
@@ -367,7 +367,7 @@ def test_c2_full_size_sampled_pixels(c2_frame):
 
 @pytest.mark.parametrize("tiling", [(1, 1), (2, 2)])
 def test_backward_matches_oracle(tiling):
-    scene, cams = scenes.config_c1()
+    scene, cams = scenes.box_2k_128()
     cam = cams[0]
     _, proj, bins = _gpu_frame(scene, cam, tiling)
     rgb, T, nc = tgs.rasterize(proj, bins, cam.width, cam.height, "fp32")
@@ -387,7 +387,7 @@ def test_backward_matches_oracle(tiling):
 
 
 def test_autograd_function():
-    scene, cams = scenes.config_c1()
+    scene, cams = scenes.box_2k_128()
     cam = cams[0]
     _, proj, bins = _gpu_frame(scene, cam, (2, 2))
     m = proj.mean2d.clone().requires_grad_(True)

@@ -152,7 +152,7 @@ def test_ewa_jacobian_clamp_outside_view(orc):
 
 
 def test_conic_inverts_dilated_covariance(orc):
-    scene, cams = scenes.config_c1()
+    scene, cams = scenes.box_2k_128()
     cam = cams[0]
     pr = orc.preprocess(scene, cam)
     for i in range(0, scene.n, 97):
@@ -335,7 +335,7 @@ def test_pruning_of_negligible_alpha(orc):
 
 def test_blend_weights_sum_to_one(orc):
     # with every colour 1 and a black background, C = sum_i T_i alpha_i = 1 - T_final
-    scene, cams = scenes.config_c1()
+    scene, cams = scenes.box_2k_128()
     pr = orc.preprocess(scene, cams[0])
     b = orc.bin_sort(pr.mean2d, pr.radius, pr.depth, 128, 128, 2, 2)
     img = orc.blend(128, 128, pr.mean2d, pr.conic, pr.opacity, np.ones_like(pr.rgb), b)
@@ -401,7 +401,7 @@ def test_grouping_is_exact(orc, gw, gh):
 
 
 def test_pixel_list_matches_full_frame(orc):
-    scene, cams = scenes.config_c1()
+    scene, cams = scenes.box_2k_128()
     pr, b, img = orc.render(scene, cams[0])
     rng = np.random.default_rng(0)
     pix = np.stack([rng.integers(0, 128, 200), rng.integers(0, 128, 200)], 1)

@@ -14,10 +14,10 @@ GB = 1 << 30
 
 
 def _scenes():
-    c1, cams = scenes.config_c1()
+    box, cams = scenes.box_2k_128()
     mix = scenes.mixture_scene(60_000, seed=7, components=16, cluster_std=0.4, radius=1.5,
                                log_scale_mean=-3.5, sh_degree=3)
-    return c1, cams[0], mix
+    return box, cams[0], mix
 
 
 def _cameras():
@@ -36,10 +36,10 @@ def _direct(ds, cam, tiling, precision):
 
 @pytest.mark.parametrize("precision,tiling", [("fp16_tc", (2, 2)), ("fp32", (1, 1))])
 def test_server_frames_equal_direct_path(precision, tiling):
-    c1, cam1, mix = _scenes()
+    box, cam1, mix = _scenes()
     cams = _cameras()
     with tgs.Server(8 * GB, max_inflight=32, slots=4, precision=precision, tiling=tiling) as srv:
-        s_c1 = srv.add_scene(tgs.DeviceScene.from_host(c1))  # device arrays
+        s_box = srv.add_scene(tgs.DeviceScene.from_host(box))  # device arrays
         s_mix = srv.add_scene(mix)                            # host arrays
         jobs = []
         for rep in range(3):
@@ -48,10 +48,10 @@ def test_server_frames_equal_direct_path(precision, tiling):
                 T = torch.empty((cam.height, cam.width), device="cuda")
                 jobs.append((srv.submit(s_mix, cam, rgb, T), "mix", cam, rgb, T))
             rgb = torch.empty((3, cam1.height, cam1.width), device="cuda")
-            jobs.append((srv.submit(s_c1, cam1, rgb, None), "c1", cam1, rgb, None))
+            jobs.append((srv.submit(s_box, cam1, rgb, None), "box", cam1, rgb, None))
         for ticket, *_ in jobs:
             assert srv.wait(ticket, 20000) == tgs.TGS_OK
-        ds = {"c1": tgs.DeviceScene.from_host(c1), "mix": tgs.DeviceScene.from_host(mix)}
+        ds = {"box": tgs.DeviceScene.from_host(box), "mix": tgs.DeviceScene.from_host(mix)}
         for _, name, cam, rgb, T in jobs:
             ref_rgb, ref_T = _direct(ds[name], cam, tiling, precision)
             assert np.array_equal(rgb.cpu().numpy(), ref_rgb)
@@ -67,9 +67,9 @@ def test_server_frames_equal_direct_path(precision, tiling):
 
 
 def test_admission_pause_wait_and_scene_removal():
-    c1, cam1, _ = _scenes()
+    box, cam1, _ = _scenes()
     with tgs.Server(2 * GB, max_inflight=3, slots=2) as srv:
-        sid = srv.add_scene(c1)
+        sid = srv.add_scene(box)
         srv.pause(True)
         bufs = [torch.empty((3, cam1.height, cam1.width), device="cuda") for _ in range(4)]
         tickets = [srv.submit(sid, cam1, bufs[k]) for k in range(3)]
@@ -96,13 +96,13 @@ def test_admission_pause_wait_and_scene_removal():
 
 
 def test_budget_limits():
-    c1, cam1, mix = _scenes()
+    box, cam1, mix = _scenes()
     # the mixture scene (60k Gaussians at SH degree 3) needs ~14 MB: too much for 4 MB
     with tgs.Server(4 << 20, max_inflight=4, slots=1) as srv:
         with pytest.raises(tgs.TgsError) as e:
             srv.add_scene(mix)
         assert e.value.status == tgs.TGS_ERR_CAPACITY
-        sid = srv.add_scene(c1)  # 2,000 Gaussians fit
+        sid = srv.add_scene(box)  # 2,000 Gaussians fit
         big = scenes.identity_camera(4096, 4096)  # its bins and workspace do not
         rgb = torch.empty((3, 4096, 4096), device="cuda")
         t = srv.submit(sid, big, rgb)

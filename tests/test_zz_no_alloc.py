@@ -26,7 +26,7 @@ def _np(t):
 
 def _case(name):
     if name == "box":
-        scene, cams = scenes.config_c1()
+        scene, cams = scenes.box_2k_128()
         return scene, cams[0], (2, 2)
     scene = scenes.mixture_scene(30_000, seed=9, components=16, cluster_std=0.3, radius=2.0,
                                  log_scale_mean=-3.8, sh_degree=3)
