@@ -127,3 +127,18 @@ def test_serve_argument_validation_is_host_side(lib):
     assert lib.tgs_serve_get_stats(None, C.byref(st)) == tgs.TGS_ERR_INVALID_ARGUMENT
     assert lib.tgs_serve_destroy(None) == tgs.TGS_ERR_INVALID_ARGUMENT
 
+
+
+def test_size_limits_are_checked_on_the_host(lib):
+    import ctypes as C
+
+    import paper_2605_17855_gb300 as tgs
+    out = C.c_size_t(0)
+    t = tgs._Tiling(2, 2)
+    # counts and capacities are limited to < 2^30 (30-bit look-back counters in the bin sort)
+    assert lib.tgs_bin_sort_workspace_size(1 << 30, 10, 64, 64, C.byref(t), C.byref(out)) == 1
+    assert lib.tgs_bin_sort_workspace_size(10, 1 << 30, 64, 64, C.byref(t), C.byref(out)) == 1
+    assert lib.tgs_bin_sort_workspace_size((1 << 30) - 1, (1 << 30) - 1, 64, 64, C.byref(t), C.byref(out)) == 0
+    # image sizes up to 16384 per side
+    assert lib.tgs_bin_sort_workspace_size(10, 10, 16385, 64, C.byref(t), C.byref(out)) == 1
+    assert lib.tgs_bin_sort_workspace_size(10, 10, 16384, 16384, C.byref(t), C.byref(out)) == 0
