@@ -71,13 +71,18 @@ def test_static_scratch_matches_workspace_on_consecutive_calls():
     assert np.array_equal(_np(got.ranges), _np(ref.ranges))
 
 
-def test_static_scratch_rejects_oversized_requests():
-    scene, cam, tiling = _case("box")
-    proj = tgs.preprocess(tgs.DeviceScene.from_host(scene), cam)
+@pytest.mark.parametrize("n,capacity,width,height,tiling", [
+    (2_000_000, 100_000, 1024, 1024, (2, 2)),   # the per-Gaussian buffers do not fit
+    (2_000, 4_000_000, 1600, 1064, (1, 1)),     # the group-id radix buffers do not fit
+])
+def test_static_scratch_rejects_oversized_requests(n, capacity, width, height, tiling):
+    assert tgs.workspace_size(n, capacity, width, height, tiling) > (16 << 20)
+    proj = tgs.Projected.empty(n, "cuda")  # refused before any kernel reads it
+    cam = scenes.identity_camera(width, height)
     lib = tgs.load()
-    big = tgs.allocate_bins(proj.n, 4_000_000, cam.width, cam.height, tiling)  # > 16 MiB of scratch
+    big = tgs.allocate_bins(n, capacity, cam.width, cam.height, tiling)
     t = tgs._Tiling(*tiling)
-    st = lib.tgs_bin_sort_static(C.byref(proj.struct()), proj.n, cam.width, cam.height, C.byref(t),
+    st = lib.tgs_bin_sort_static(C.byref(proj.struct()), n, cam.width, cam.height, C.byref(t),
                                  C.byref(big.struct()), None, None)
     assert st == tgs.TGS_ERR_CAPACITY
     assert b"static area holds" in lib.tgs_last_error_message()
