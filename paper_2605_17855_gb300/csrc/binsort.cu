@@ -739,9 +739,11 @@ tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int h
         dslices, visible, L.cells, dsum);
     TGS_CHECK_LAUNCH("k_group_reduce");
   }
+  // the attribute is the kernel's largest request, not this call's: CUDA graphs captured for other
+  // image sizes launch the same function with their own sizes
   const int table_smem = L.sliced ? 4 * L.cells : 0;
   TGS_CUDA(cudaFuncSetAttribute(k_group_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                table_smem));
+                                4 * kMaxSmemCells));
   k_group_table<<<1, kTableThreads, table_smem, st>>>(
       dsum, GX, GY, L.sliced ? 1 : 0, b.num_entries, cap, passes, b.ranges, hist_g);
   TGS_CHECK_LAUNCH("k_group_table");
