@@ -26,7 +26,8 @@
 //     cannot reach at alpha >= 1/255).
 //   * MMA thread: per tile, D[128 px x 32] = A_h[128 x 16] * B_t[32 x 16]^T with
 //     tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 32, K = 16), FP32 accumulators in tensor
-//     memory, double-buffered; completion signalled through tcgen05.commit on mbarriers.
+//     memory in NST stages (two, or one when two CTAs share an SM); completion signalled through
+//     tcgen05.commit on mbarriers.
 //   * epilogue warpgroups (one per tile of a round): each thread owns one TMEM lane = one pixel in
 //     each of the tile's two 128-pixel M blocks, streams the tile's exponents out of tensor memory
 //     8 columns at a time (the next load in flight while the current columns are blended) and runs
@@ -65,8 +66,9 @@ constexpr int NB = 32;     // list entries per chunk = MMA N
 
 __device__ __forceinline__ float inf_f() { return __int_as_float(0x7f800000); }
 
-template <int GW, int GH, int NWG, int NPROD>
+template <int GW, int GH, int NWG, int NPROD, int NST = 2>
 struct Cfg {
+  static constexpr int kStages = NST;  // accumulator stages in tensor memory
   static constexpr int kTiles = GW * GH;
   static constexpr int kRounds = kTiles / NWG;
   static_assert(kTiles % NWG == 0, "tiles must split evenly over warpgroups");
@@ -76,7 +78,7 @@ struct Cfg {
   static constexpr int kThreads = 32 * (kMmaWarp + 1);
   static constexpr int kSlots = 2 * NPROD;  // chunk c uses slot c % kSlots, produced by c % NPROD
   static constexpr int kStageCols = NWG * 2 * NB;
-  static constexpr int kTmemCols = 2 * kStageCols;
+  static constexpr int kTmemCols = NST * kStageCols;
   static_assert(kTmemCols == 32 || kTmemCols == 64 || kTmemCols == 128 || kTmemCols == 256 ||
                     kTmemCols == 512,
                 "TMEM allocation must be a power of two in [32, 512]");
@@ -254,15 +256,15 @@ __device__ __forceinline__ void blend_granule(const uint32_t (&d)[16], int g, in
   }
 }
 
-template <int GW, int GH, int NWG, int NPROD, bool BF, bool COUNT, bool NC>
-__global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD>::kThreads, 1)
+template <int GW, int GH, int NWG, int NPROD, int NST, bool BF, bool COUNT, bool NC>
+__global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NST)
     k_raster_tc(const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ vals,
                 const uint16_t* __restrict__ masks, const float2* __restrict__ mean2d,
                 const float4* __restrict__ conic_opacity, const float* __restrict__ rgb, int width,
                 int height, int GX, float3 bg, float* __restrict__ out_rgb,
                 float* __restrict__ out_T, int* __restrict__ n_contrib,
                 unsigned long long* __restrict__ counters, int32_t* __restrict__ err, int cull) {
-  using C = Cfg<GW, GH, NWG, NPROD>;
+  using C = Cfg<GW, GH, NWG, NPROD, NST>;
   constexpr int TILES = C::kTiles;
   constexpr int SLOTS = C::kSlots;
   constexpr int KB = BF ? 2 : 1;  // K blocks of 16: FP16 hi|lo, or BF16 hi|mid then lo
@@ -494,8 +496,8 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD>::kThreads, 1)
         }
         auto& sl = S.slot[s];
         for (int r = 0; r < C::kRounds; ++r, ++job) {
-          const int st = job & 1;
-          if (!mbar_wait_bounded(&S.tempty[st], ((job >> 1) & 1) ^ 1, abort_flag, kWaitLimitNs)) {
+          const int st = job % NST;
+          if (!mbar_wait_bounded(&S.tempty[st], ((job / NST) & 1) ^ 1, abort_flag, kWaitLimitNs)) {
             failed = true;
             break;
           }
@@ -523,8 +525,8 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD>::kThreads, 1)
         record_abort(&S.abort, err);
       } else {
         // end signal: complete the next tfull phase with a plain arrive after publishing its index
-        const int st = job & 1;
-        if (mbar_wait_bounded(&S.tempty[st], ((job >> 1) & 1) ^ 1, abort_flag, kWaitLimitNs)) {
+        const int st = job % NST;
+        if (mbar_wait_bounded(&S.tempty[st], ((job / NST) & 1) ^ 1, abort_flag, kWaitLimitNs)) {
           *reinterpret_cast<volatile int*>(&S.end_job) = job;
           mbar_arrive(&S.tfull[st]);
         } else {
@@ -564,8 +566,8 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD>::kThreads, 1)
       const int s = c % SLOTS;
 #pragma unroll
       for (int r = 0; r < C::kRounds; ++r) {
-        const int st = job & 1;
-        bool ok = mbar_wait_bounded(&S.tfull[st], (job >> 1) & 1, abort_flag, kWaitLimitNs);
+        const int st = job % NST;
+        bool ok = mbar_wait_bounded(&S.tfull[st], (job / NST) & 1, abort_flag, kWaitLimitNs);
         if (!__all_sync(0xffffffffu, ok)) { record_abort(&S.abort, err); finished = true; break; }
         if (__shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(&S.end_job), 0) == job) {
           finished = true;
@@ -589,36 +591,54 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD>::kThreads, 1)
           const int base = sl.base;
           const int tx = gx * GW + (t % GW), ty = gy * GH + (t / GW);
           const int ngr = (cnt + 7) >> 3;  // 8-column granules holding the packed entries
-          uint32_t ga[16], gb[16];
-          __syncwarp();
-          tmem_ld8x2_async(taddr, taddr + NB, ga);
-          tmem_wait_ld(ga);
-          // granule g is blended while granule g + 1 is loading; the stage is released once its
-          // last load has completed
-          for (int g = 0; g < ngr; g += 2) {
-            if (g + 1 < ngr) {
+          if constexpr (NST == 1) {
+            // one accumulator stage (two CTAs per SM): granules load one at a time, the other
+            // CTA's warps hide the latency
+            for (int g = 0; g < ngr; ++g) {
+              uint32_t ga[16];
               __syncwarp();
-              tmem_ld8x2_async(taddr + 8 * (g + 1), taddr + NB + 8 * (g + 1), gb);
-            } else {
-              tc_fence_before();
-              __syncwarp();
-              if (lane == 0) mbar_arrive(&S.tempty[st]);
-            }
-            blend_granule<TILES, KB, COUNT, NC>(ga, g, cnt, sb, base, sl, t, tx, ty, quarter, lane,
-                                        ps[r][0], ps[r][1], evaluated, passing, slots);
-            if (g + 1 < ngr) {
-              tmem_wait_ld(gb);
-              if (g + 2 < ngr) {
+              tmem_ld8x2_async(taddr + 8 * g, taddr + NB + 8 * g, ga);
+              tmem_wait_ld(ga);
+              if (g + 1 == ngr) {
+                tc_fence_before();
                 __syncwarp();
-                tmem_ld8x2_async(taddr + 8 * (g + 2), taddr + NB + 8 * (g + 2), ga);
+                if (lane == 0) mbar_arrive(&S.tempty[st]);
+              }
+              blend_granule<TILES, KB, COUNT, NC>(ga, g, cnt, sb, base, sl, t, tx, ty, quarter, lane,
+                                                  ps[r][0], ps[r][1], evaluated, passing, slots);
+            }
+          } else {
+            uint32_t ga[16], gb[16];
+            __syncwarp();
+            tmem_ld8x2_async(taddr, taddr + NB, ga);
+            tmem_wait_ld(ga);
+            // granule g is blended while granule g + 1 is loading; the stage is released once its
+            // last load has completed
+            for (int g = 0; g < ngr; g += 2) {
+              if (g + 1 < ngr) {
+                __syncwarp();
+                tmem_ld8x2_async(taddr + 8 * (g + 1), taddr + NB + 8 * (g + 1), gb);
               } else {
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&S.tempty[st]);
               }
-              blend_granule<TILES, KB, COUNT, NC>(gb, g + 1, cnt, sb, base, sl, t, tx, ty, quarter, lane,
+              blend_granule<TILES, KB, COUNT, NC>(ga, g, cnt, sb, base, sl, t, tx, ty, quarter, lane,
                                           ps[r][0], ps[r][1], evaluated, passing, slots);
-              if (g + 2 < ngr) tmem_wait_ld(ga);
+              if (g + 1 < ngr) {
+                tmem_wait_ld(gb);
+                if (g + 2 < ngr) {
+                  __syncwarp();
+                  tmem_ld8x2_async(taddr + 8 * (g + 2), taddr + NB + 8 * (g + 2), ga);
+                } else {
+                  tc_fence_before();
+                  __syncwarp();
+                  if (lane == 0) mbar_arrive(&S.tempty[st]);
+                }
+                blend_granule<TILES, KB, COUNT, NC>(gb, g + 1, cnt, sb, base, sl, t, tx, ty, quarter, lane,
+                                            ps[r][0], ps[r][1], evaluated, passing, slots);
+                if (g + 2 < ngr) tmem_wait_ld(ga);
+              }
             }
           }
           wdone[r] = __all_sync(0xffffffffu, ps[r][0].thr == inf_f() && ps[r][1].thr == inf_f());
@@ -684,11 +704,11 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD>::kThreads, 1)
   if (warp == C::kMmaWarp) tmem_dealloc(tmem, C::kTmemCols);
 }
 
-template <bool BF, int GW, int GH, int NWG, int NPROD>
+template <bool BF, int GW, int GH, int NWG, int NPROD, int NST = 2>
 tgs_status launch_cfg(const tgs_projected& p, const tgs_bins& b, int width, int height,
                       const tgs_raster_opts& o, float* out_rgb, float* out_T, int32_t* n_contrib,
                       cudaStream_t st) {
-  using Cf = Cfg<GW, GH, NWG, NPROD>;
+  using Cf = Cfg<GW, GH, NWG, NPROD, NST>;
   using Sm = Smem<GW * GH, Cf::kSlots, BF ? 2 : 1>;
   static_assert(sizeof(Sm) + 1024 <= 227 * 1024, "shared memory of one CTA exceeds 227 KB");
   const int TX = div_up(width, kTile), TY = div_up(height, kTile);
@@ -717,11 +737,11 @@ tgs_status launch_cfg(const tgs_projected& p, const tgs_bins& b, int width, int 
   };
   tgs_status s;
   if (count)
-    s = n_contrib ? launch(k_raster_tc<GW, GH, NWG, NPROD, BF, true, true>)
-                  : launch(k_raster_tc<GW, GH, NWG, NPROD, BF, true, false>);
+    s = n_contrib ? launch(k_raster_tc<GW, GH, NWG, NPROD, NST, BF, true, true>)
+                  : launch(k_raster_tc<GW, GH, NWG, NPROD, NST, BF, true, false>);
   else
-    s = n_contrib ? launch(k_raster_tc<GW, GH, NWG, NPROD, BF, false, true>)
-                  : launch(k_raster_tc<GW, GH, NWG, NPROD, BF, false, false>);
+    s = n_contrib ? launch(k_raster_tc<GW, GH, NWG, NPROD, NST, BF, false, true>)
+                  : launch(k_raster_tc<GW, GH, NWG, NPROD, NST, BF, false, false>);
   if (s != TGS_OK) return s;
   TGS_CHECK_LAUNCH("k_raster_tc");
   return TGS_OK;
@@ -735,10 +755,15 @@ tgs_status launch_raster_tc_typed(const tgs_projected& p, const tgs_bins& b, int
                                   float* out_T, int32_t* n_contrib, cudaStream_t st) {
   if (((uintptr_t)p.mean2d & 7) || ((uintptr_t)p.conic_opacity & 15))
     return set_error("mean2d needs 8-byte and conic_opacity 16-byte alignment"), TGS_ERR_INVALID_ARGUMENT;
+  // FP16 groups of up to 8 tiles: one accumulator stage of 256 tensor-memory columns and at most
+  // 48 registers, so that two CTAs share an SM and hide each other's latency (measured faster than
+  // one CTA with two stages); 1x1 (not limited by tensor memory), 4x4 and BF16 (shared memory for
+  // two CTAs) keep two stages
+  constexpr int NST = BF ? 2 : 1;
   if (gw == 1 && gh == 1) return launch_cfg<BF, 1, 1, 1, 2>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
-  if (gw == 2 && gh == 2) return launch_cfg<BF, 2, 2, 4, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
-  if (gw == 4 && gh == 2) return launch_cfg<BF, 4, 2, 4, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
-  if (gw == 2 && gh == 4) return launch_cfg<BF, 2, 4, 4, 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
+  if (gw == 2 && gh == 2) return launch_cfg<BF, 2, 2, 4, 3, NST>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
+  if (gw == 4 && gh == 2) return launch_cfg<BF, 4, 2, 4, 3, NST>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
+  if (gw == 2 && gh == 4) return launch_cfg<BF, 2, 4, 4, 3, NST>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
   // 4x4 BF16: two producers (four slots), so that the doubled coefficient tiles fit in shared memory
   if (gw == 4 && gh == 4)
     return launch_cfg<BF, 4, 4, 4, BF ? 2 : 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
