@@ -207,25 +207,25 @@ __device__ __forceinline__ void blend_column(float e0, float e1, int j, int base
   blend_step<COUNT, NC>(e1, rc, s1, pos, passing);
 }
 
-// Blends one 8-column granule (packed entries 8g .. 8g+7 of tile t) into the thread's two pixels.
-// d[0..7] are pixel 0's exponents, d[8..15] pixel 1's. The steps are predicated, not branched per
-// column, so the exponentials and tests of different columns and pixels overlap; a granule that
-// is cut by the end of the tile's packed entries only runs its valid columns.
-template <int TILES, int KB, bool COUNT, bool NC>
-__device__ __forceinline__ void blend_granule(const uint32_t (&d)[16], int g, int cnt, uint32_t sb,
+// Blends one granule of W columns (packed entries W g .. W g + W - 1 of tile t) into the thread's
+// two pixels. d[0..W-1] are pixel 0's exponents, d[W..2W-1] pixel 1's. The steps are predicated,
+// not branched per column, so the exponentials and tests of different columns and pixels overlap;
+// a granule that is cut by the end of the tile's packed entries only runs its valid columns.
+template <int TILES, int KB, bool COUNT, bool NC, int W = 8>
+__device__ __forceinline__ void blend_granule(const uint32_t (&d)[2 * W], int g, int cnt, uint32_t sb,
                                               int base, const Slot<TILES, KB>& sl, int t, int tx,
                                               int ty, int quarter, int lane, PixState& s0,
                                               PixState& s1, unsigned long long& evaluated,
                                               unsigned long long& passing,
                                               unsigned long long& slots) {
-  if (COUNT) slots += 16;
-  float e0[8], e1[8];
+  if (COUNT) slots += 2 * W;
+  float e0[W], e1[W];
 #pragma unroll
-  for (int jj = 0; jj < 8; ++jj) {
+  for (int jj = 0; jj < W; ++jj) {
     e0[jj] = __uint_as_float(d[jj]);
-    e1[jj] = __uint_as_float(d[8 + jj]);
+    e1[jj] = __uint_as_float(d[W + jj]);
   }
-  const uint32_t sbg = (sb >> (8 * g)) & 0xffu;
+  const uint32_t sbg = (sb >> (W * g)) & ((1u << W) - 1u);
   if (sbg) {  // rare: rows whose FP16 coefficients would be too inaccurate
     int lx0, ly0, lx1, ly1;
     lane_pixel(0, quarter * 32 + lane, lx0, ly0);
@@ -233,26 +233,26 @@ __device__ __forceinline__ void blend_granule(const uint32_t (&d)[16], int g, in
     const float px0 = (float)(tx * kTile + lx0), py0 = (float)(ty * kTile + ly0);
     const float px1 = (float)(tx * kTile + lx1), py1 = (float)(ty * kTile + ly1);
 #pragma unroll
-    for (int jj = 0; jj < 8; ++jj)
+    for (int jj = 0; jj < W; ++jj)
       if ((sbg >> jj) & 1u) {
-        const int en = sl.entry[t][8 * g + jj];
+        const int en = sl.entry[t][W * g + jj];
         const float2 es = scalar_exponents(px0, py0, px1, py1, sl.sp0[en], sl.sp1[en]);
         e0[jj] = es.x;
         e1[jj] = es.y;
       }
   }
-  const int ncols = cnt - 8 * g;  // >= 1; warp-uniform
-  if (ncols >= 8) {
+  const int ncols = cnt - W * g;  // >= 1; warp-uniform
+  if (ncols >= W) {
 #pragma unroll
-    for (int jj = 0; jj < 8; ++jj)
-      blend_column<TILES, KB, COUNT, NC>(e0[jj], e1[jj], 8 * g + jj, base, sl, t, s0, s1, evaluated,
-                                     passing);
+    for (int jj = 0; jj < W; ++jj)
+      blend_column<TILES, KB, COUNT, NC>(e0[jj], e1[jj], W * g + jj, base, sl, t, s0, s1, evaluated,
+                                         passing);
   } else {
 #pragma unroll
-    for (int jj = 0; jj < 7; ++jj)
+    for (int jj = 0; jj < W - 1; ++jj)
       if (jj < ncols)
-        blend_column<TILES, KB, COUNT, NC>(e0[jj], e1[jj], 8 * g + jj, base, sl, t, s0, s1, evaluated,
-                                       passing);
+        blend_column<TILES, KB, COUNT, NC>(e0[jj], e1[jj], W * g + jj, base, sl, t, s0, s1, evaluated,
+                                           passing);
   }
 }
 
@@ -343,13 +343,10 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
     struct Gathered {
       float2 mu;
       float4 co;
-      float3 col;
     };
     auto gather = [&](uint32_t idx, bool valid, Gathered& g) {
       g.mu = valid ? mean2d[idx] : make_float2(0.f, 0.f);
       g.co = valid ? conic_opacity[idx] : make_float4(0.f, 0.f, 0.f, 1.f);
-      g.col = valid ? make_float3(rgb[3 * idx], rgb[3 * idx + 1], rgb[3 * idx + 2])
-                    : make_float3(0.f, 0.f, 0.f);
     };
     int c = warp - C::kProdWarp0;
     uint32_t idx_a, msk_a, idx_b, msk_b;
@@ -373,6 +370,8 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
         break;
       }
       auto& sl = S.slot[s];
+      const float3 colr = val_a ? make_float3(rgb[3 * idx_a], rgb[3 * idx_a + 1], rgb[3 * idx_a + 2])
+                                : make_float3(0.f, 0.f, 0.f);
       const bool valid = val_a;
       const uint32_t msk = msk_a;
       const float2 mu = g_a.mu;
@@ -388,7 +387,7 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
         const float dp = fmaxf(det, 0.f);
         Lc = make_float3(co.x * inv, co.y * inv, dp > 0.f ? dp * rsqrtf(dp) * inv : 0.f);
       }
-      const float4 rgbc = make_float4(g_a.col.x, g_a.col.y, g_a.col.z, fminf(lo2, kLog2AlphaMax));
+      const float4 rgbc = make_float4(colr.x, colr.y, colr.z, fminf(lo2, kLog2AlphaMax));
       sl.sp0[lane] = make_float4(mu.x, mu.y, Lc.x, Lc.y);
       sl.sp1[lane] = make_float2(Lc.z, lo2);
 #pragma unroll
@@ -474,6 +473,7 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
       if (lane == 0) mbar_arrive(&S.full[s]);
       // rotate the pipeline
       g_a = g_b;
+      idx_a = idx_b;
       msk_a = msk_b;
       val_a = val_b;
       idx_b = idx_c;
@@ -594,18 +594,21 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
           if constexpr (NST == 1) {
             // one accumulator stage (two CTAs per SM): granules load one at a time, the other
             // CTA's warps hide the latency
-            for (int g = 0; g < ngr; ++g) {
-              uint32_t ga[16];
+            // granules of 4 columns (8 registers), so that the epilogue fits the 48-register cap
+            const int ngr4 = (cnt + 3) >> 2;
+            for (int g = 0; g < ngr4; ++g) {
+              uint32_t ga[8];
               __syncwarp();
-              tmem_ld8x2_async(taddr + 8 * g, taddr + NB + 8 * g, ga);
-              tmem_wait_ld(ga);
-              if (g + 1 == ngr) {
+              tmem_ld4x2_async(taddr + 4 * g, taddr + NB + 4 * g, ga);
+              tmem_wait_ld8(ga);
+              if (g + 1 == ngr4) {
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&S.tempty[st]);
               }
-              blend_granule<TILES, KB, COUNT, NC>(ga, g, cnt, sb, base, sl, t, tx, ty, quarter, lane,
-                                                  ps[r][0], ps[r][1], evaluated, passing, slots);
+              blend_granule<TILES, KB, COUNT, NC, 4>(ga, g, cnt, sb, base, sl, t, tx, ty, quarter,
+                                                     lane, ps[r][0], ps[r][1], evaluated, passing,
+                                                     slots);
             }
           } else {
             uint32_t ga[16], gb[16];

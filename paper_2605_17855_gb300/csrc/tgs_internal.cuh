@@ -130,6 +130,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// As mbar_try_wait, with a hint of how long (ns) the thread may stay suspended waiting for the
+// phase before the call returns false; a suspended warp issues no instructions.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity,
+                                                   uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
 // Non-blocking test of an mbarrier phase.
 __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
@@ -147,13 +161,19 @@ __device__ __forceinline__ void mbar_arrive_n(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
                : "memory");
 }
+// Longest suspension of one try-wait inside the bounded waits below; the abort flag and the time
+// limit are checked between them.
+constexpr uint32_t kSuspendHintNs = 20000;
+// The same for waits that a stop flag can end: the flag is no barrier event, so a suspended waiter
+// sees it only when the hint expires.
+constexpr uint32_t kStopHintNs = 1000;
 // Bounded wait: gives up after `limit_ns` (or when *abort is set) and returns false.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   volatile int* abort, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
   while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_hint(bar, parity, kSuspendHintNs)) return true;
     if (*abort) return false;
     if (globaltimer_ns() - t0 > limit_ns) return false;
   }
@@ -166,7 +186,7 @@ __device__ __forceinline__ int mbar_wait_or_stop(uint64_t* bar, uint32_t parity,
   if (mbar_try_wait(bar, parity)) return 0;
   const uint64_t t0 = globaltimer_ns();
   while (true) {
-    if (mbar_try_wait(bar, parity)) return 0;
+    if (mbar_try_wait_hint(bar, parity, kStopHintNs)) return 0;
     if (*stop) return 1;
     if (*abort) return 2;
     if (globaltimer_ns() - t0 > limit_ns) return 2;
@@ -260,6 +280,16 @@ __device__ __forceinline__ void tmem_ld8_async(uint32_t ta, uint32_t (&r)[8]) {
                : "=r"(r[0]),"=r"(r[1]),"=r"(r[2]),"=r"(r[3]),"=r"(r[4]),"=r"(r[5]),"=r"(r[6]),"=r"(r[7])
                : "r"(ta)
                : "memory");
+}
+// Two tensor-memory loads of 4 consecutive columns each (pixel blocks at ta and tb) into r[0..3] and
+// r[4..7], without waiting; read them only after tmem_wait_ld8(r).
+__device__ __forceinline__ void tmem_ld4x2_async(uint32_t ta, uint32_t tb, uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%8];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4,%5,%6,%7}, [%9];"
+      : "=r"(r[0]),"=r"(r[1]),"=r"(r[2]),"=r"(r[3]),"=r"(r[4]),"=r"(r[5]),"=r"(r[6]),"=r"(r[7])
+      : "r"(ta), "r"(tb)
+      : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld8(uint32_t (&r)[8]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]),"+r"(r[1]),"+r"(r[2]),"+r"(r[3]),"+r"(r[4]),"+r"(r[5]),"+r"(r[6]),"+r"(r[7]) : : "memory");
