@@ -1,11 +1,14 @@
 // Grouped tensor-core rasterizer (Section 4.2 "Tensorizing the power computation" and Section 4.4.2
 // "Grouped rasterization"; Algorithm 1, the per-group CTA loop), written for sm_103a with tcgen05.
 //
-// One CTA per tile group. The group's depth-sorted list is consumed in chunks of NB = 32 entries:
-//   * producer warps (several, on interleaved chunks): gather the chunk's Gaussians (mean, conic,
-//     opacity, colour, mask). For every member tile, the entries whose mask bit is set are packed
-//     to the front (Section 4.4.2: "select Gaussian entries whose bit mask includes t"), and for
-//     each the producer writes the Gaussian's coefficient row of the power expansion about the
+// One CTA per tile group. The group's depth-sorted list is read in chunks of NB = 32 entries and
+// consumed as jobs of up to NB packed rows per tile:
+//   * producer warps (several, on interleaved super-chunks of kSuper chunks): gather a chunk's
+//     Gaussians (mean, conic, opacity, colour, mask). For every member tile, the entries whose mask
+//     bit is set are appended to the tile's rows of the open job (Section 4.4.2: "select Gaussian
+//     entries whose bit mask includes t"); a job spans chunks until a tile's NB rows would
+//     overflow, so jobs stay dense after the tile skip below. For each packed entry the producer
+//     writes the Gaussian's coefficient row of the power expansion about the
 //     tile's centre (o_x, o_y) = (16 tx + 8, 16 ty + 8). With pixel offsets (x, y) = (px - o_x,
 //     py - o_y) and (mx, my) = mu' - o:
 //        log2(o) + log2(e) * power = q . [x^2, xy, y^2, x, y, 1]
@@ -33,10 +36,10 @@
 //     8 columns at a time (the next load in flight while the current columns are blended) and runs
 //     the front-to-back blend of Section 2 in FP32: skip if alpha < 1/255 (tested in the log2
 //     domain before the exp), alpha = min(0.99, 2^D), stop when T' < 1e-4 without blending.
-// The chunk is loaded from global memory once per group and reused by all member tiles
+// Each chunk is loaded from global memory once per group and reused by all member tiles
 // (the cross-tile reuse of Section 4.4.2); packing a tile's entries keeps their order, hence each
 // tile's front-to-back order (Section 4.4.2, numerical equivalence with per-tile rasterization).
-// Termination: before each chunk the MMA thread checks whether every epilogue warp has finished
+// Termination: before each job the MMA thread checks whether every epilogue warp has finished
 // all its pixels (T < 1e-4 or end of list); if so it stops issuing, raises a stop flag for the
 // producers and signals the epilogue the index of the last job.
 // Every wait on an mbarrier is bounded (2 s); on expiry the CTA records TGS_ERR_TIMEOUT in the
@@ -63,6 +66,26 @@ constexpr float kCullMargin = 0.01f;
 constexpr int kLBO = 128;  // bytes between the two K core matrices of an 8-row group
 constexpr int kSBO = 256;  // bytes between 8-row groups
 constexpr int NB = 32;     // list entries per chunk = MMA N
+// Chunks per super-chunk: the unit a producer packs into its own jobs (a job spans chunks until a
+// tile's NB rows are full), so that jobs stay dense after the tile skip.
+constexpr int kSuper = 2;
+// Job slots per producer for groups of up to four tiles.
+constexpr int kRingSmall = 2;
+
+// Job counters of the producers' rings, kept in registers (p is warp-uniform).
+template <int N>
+__device__ __forceinline__ int ring_get(const int (&k)[N], int p) {
+  int v = k[0];
+#pragma unroll
+  for (int i = 1; i < N; ++i)
+    if (p == i) v = k[i];
+  return v;
+}
+template <int N>
+__device__ __forceinline__ void ring_inc(int (&k)[N], int p) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) k[i] += (p == i) ? 1 : 0;
+}
 
 __device__ __forceinline__ float inf_f() { return __int_as_float(0x7f800000); }
 
@@ -76,7 +99,9 @@ struct Cfg {
   static constexpr int kProdWarp0 = kEpiWarps;
   static constexpr int kMmaWarp = kEpiWarps + NPROD;
   static constexpr int kThreads = 32 * (kMmaWarp + 1);
-  static constexpr int kSlots = 2 * NPROD;  // chunk c uses slot c % kSlots, produced by c % NPROD
+  // each producer has a ring of kRing job slots (deeper for small groups, whose slots are small)
+  static constexpr int kRing = GW * GH <= 4 ? kRingSmall : 2;
+  static constexpr int kSlots = kRing * NPROD;
   static constexpr int kStageCols = NWG * 2 * NB;
   static constexpr int kTmemCols = NST * kStageCols;
   static_assert(kTmemCols == 32 || kTmemCols == 64 || kTmemCols == 128 || kTmemCols == 256 ||
@@ -89,12 +114,12 @@ struct __align__(16) Slot {
   uint8_t B[TILES][KB][NB * 32];  // per tile and K block of 16, packed rows; K-major canonical,
                                   // no swizzle: (row/8)*256 + (k/8)*128 + (row%8)*16
   float4 rgbc[TILES][NB];     // packed entry k of tile t: colour, min(log2 o, log2 0.99)
-  float4 sp0[NB];             // chunk entry: mu'x, mu'y, l11, l12 (scalar rows; conic factor)
-  float2 sp1[NB];             // l22, log2 o
-  uint8_t entry[TILES][NB];   // chunk entry (0..31) of packed entry k of tile t
+  uint32_t gidx[TILES][NB];   // Gaussian of packed entry k of tile t (read for scalar rows only)
+  uint16_t rel[TILES][NB];    // list position of packed entry k of tile t, relative to `base`
   uint32_t cnt[TILES];        // packed entries of tile t
   uint32_t sbits[TILES];      // bit k: packed entry k of tile t uses the scalar path
-  int32_t base;               // list position of chunk entry 0 relative to the group start
+  int32_t base;               // list position (from the group start) of the job's first chunk
+  int32_t last;               // the job closes its super-chunk
 };
 
 template <int TILES, int SLOTS, int KB>
@@ -163,12 +188,24 @@ __device__ __forceinline__ float box_min_quadratic(float a, float b, float c, fl
   return m;
 }
 
-// Scalar FP32 exponents of a packed entry whose FP16 coefficients would be too inaccurate.
+// Cholesky factor (l11, l12, l22) of the conic [a b; b c], conic = L^T L with L = [l11 l12; 0 l22]:
+// from the hardware reciprocal square root, the determinant by Kahan's scheme.
+__device__ __forceinline__ float3 conic_cholesky(float4 co) {
+  const float inv = rsqrtf(co.x);
+  const float w2 = co.y * co.y;
+  const float det = fmaf(co.x, co.z, -w2) + fmaf(-co.y, co.y, w2);
+  const float dp = fmaxf(det, 0.f);
+  return make_float3(co.x * inv, co.y * inv, dp > 0.f ? dp * rsqrtf(dp) * inv : 0.f);
+}
+
+// Scalar FP32 exponents of a packed entry whose FP16 coefficients would be too inaccurate: the
+// Gaussian's mean and conic are read again and the power evaluated through the conic's factor.
 __device__ __noinline__ float2 scalar_exponents(float px0, float py0, float px1, float py1,
-                                                float4 p0, float2 p1) {
-  const float3 L = make_float3(p0.z, p0.w, p1.x);
-  const float e0 = fmaf(power_fp32(L, __fsub_rn(px0, p0.x), __fsub_rn(py0, p0.y)), kLog2e, p1.y);
-  const float e1 = fmaf(power_fp32(L, __fsub_rn(px1, p0.x), __fsub_rn(py1, p0.y)), kLog2e, p1.y);
+                                                float2 mu, float4 co) {
+  const float3 L = conic_cholesky(co);
+  const float lo2 = lg2(co.w);
+  const float e0 = fmaf(power_fp32(L, __fsub_rn(px0, mu.x), __fsub_rn(py0, mu.y)), kLog2e, lo2);
+  const float e1 = fmaf(power_fp32(L, __fsub_rn(px1, mu.x), __fsub_rn(py1, mu.y)), kLog2e, lo2);
   return make_float2(e0, e1);
 }
 
@@ -202,7 +239,7 @@ __device__ __forceinline__ void blend_column(float e0, float e1, int j, int base
                                              unsigned long long& passing) {
   if (COUNT) evaluated += (s0.thr < inf_f()) + (s1.thr < inf_f());
   const float4 rc = sl.rgbc[t][j];
-  const int pos = NC ? base + (int)sl.entry[t][j] + 1 : 0;
+  const int pos = NC ? base + (int)sl.rel[t][j] + 1 : 0;
   blend_step<COUNT, NC>(e0, rc, s0, pos, passing);
   blend_step<COUNT, NC>(e1, rc, s1, pos, passing);
 }
@@ -214,7 +251,9 @@ __device__ __forceinline__ void blend_column(float e0, float e1, int j, int base
 template <int TILES, int KB, bool COUNT, bool NC, int W = 8>
 __device__ __forceinline__ void blend_granule(const uint32_t (&d)[2 * W], int g, int cnt, uint32_t sb,
                                               int base, const Slot<TILES, KB>& sl, int t, int tx,
-                                              int ty, int quarter, int lane, PixState& s0,
+                                              int ty, int quarter, int lane,
+                                              const float2* __restrict__ mean2d,
+                                              const float4* __restrict__ conic_opacity, PixState& s0,
                                               PixState& s1, unsigned long long& evaluated,
                                               unsigned long long& passing,
                                               unsigned long long& slots) {
@@ -235,8 +274,8 @@ __device__ __forceinline__ void blend_granule(const uint32_t (&d)[2 * W], int g,
 #pragma unroll
     for (int jj = 0; jj < W; ++jj)
       if ((sbg >> jj) & 1u) {
-        const int en = sl.entry[t][W * g + jj];
-        const float2 es = scalar_exponents(px0, py0, px1, py1, sl.sp0[en], sl.sp1[en]);
+        const uint32_t gi = sl.gidx[t][W * g + jj];
+        const float2 es = scalar_exponents(px0, py0, px1, py1, mean2d[gi], conic_opacity[gi]);
         e0[jj] = es.x;
         e1[jj] = es.y;
       }
@@ -330,13 +369,22 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
   const int nchunks = (int)((list_end - list_start + NB - 1) / NB);
 
   if (warp >= C::kProdWarp0 && warp < C::kMmaWarp) {
-    // ---- producers: gather, pack per tile, coefficient rows; chunks c = p, p + NPROD, ... -------
-    // Software pipeline, two chunks deep: while chunk c is packed, the Gaussian gathers of chunk
-    // c + NPROD and the index/mask loads of chunk c + 2 NPROD are in flight.
+    // ---- producers: gather, pack per tile, coefficient rows -------------------------------------
+    // The list is cut into chunks of NB entries and the chunks into super-chunks of kSuper;
+    // producer p takes super-chunks p, p + NPROD, ... . It packs the surviving entries of its
+    // consecutive chunks into a job in its own ring of two slots until a tile's NB rows would
+    // overflow, then closes the job and opens the next; the last job of a super-chunk is flagged.
+    // Consumers take the super-chunks in order, so each tile still sees its entries in list
+    // order. Software pipeline: the gathers of the next chunk and the index/mask loads of the one
+    // after it are in flight while a chunk is packed.
+    const int p = warp - C::kProdWarp0;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    auto load_index = [&](int c, uint32_t& idx, uint32_t& msk, bool& valid) {
-      const uint32_t e = list_start + (uint32_t)c * NB + lane;
-      valid = c < nchunks && e < list_end;
+    auto chunk_of = [&](int u) {  // the u-th chunk of this producer
+      return (p + (u / kSuper) * NPROD) * kSuper + u % kSuper;
+    };
+    auto load_index = [&](int q, uint32_t& idx, uint32_t& msk, bool& valid) {
+      const uint32_t e = list_start + (uint32_t)q * NB + lane;
+      valid = q < nchunks && e < list_end;
       idx = valid ? vals[e] : 0u;
       msk = valid ? (uint32_t)masks[e] : 0u;
     };
@@ -348,28 +396,52 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
       g.mu = valid ? mean2d[idx] : make_float2(0.f, 0.f);
       g.co = valid ? conic_opacity[idx] : make_float4(0.f, 0.f, 0.f, 1.f);
     };
-    int c = warp - C::kProdWarp0;
-    uint32_t idx_a, msk_a, idx_b, msk_b;
-    bool val_a, val_b;
-    load_index(c, idx_a, msk_a, val_a);
-    Gathered g_a;
-    gather(idx_a, val_a, g_a);
-    load_index(c + NPROD, idx_b, msk_b, val_b);
-    for (; c < nchunks; c += NPROD) {
-      Gathered g_b;
-      gather(idx_b, val_b, g_b);  // chunk c + NPROD
-      uint32_t idx_c, msk_c;
-      bool val_c;
-      load_index(c + 2 * NPROD, idx_c, msk_c, val_c);
-      const int s = c % SLOTS;
-      const int w = mbar_wait_or_stop(&S.empty[s], ((c / SLOTS) & 1) ^ 1, stop_flag, abort_flag,
+    int k = 0;  // jobs opened in this producer's ring
+    int s = 0;  // slot of the open job
+    // waits for the next slot of the ring and starts a job at chunk q; false: stopped or timed out
+    auto open_job = [&](int q) -> bool {
+      s = C::kRing * p + k % C::kRing;
+      const int w = mbar_wait_or_stop(&S.empty[s], ((k / C::kRing) & 1) ^ 1, stop_flag, abort_flag,
                                       kWaitLimitNs);
       const unsigned wmax = __reduce_max_sync(0xffffffffu, (unsigned)w);
-      if (wmax != 0u) {  // stopped (not an error) or timed out
+      if (wmax != 0u) {
         if (wmax == 2u) record_abort(&S.abort, err);
-        break;
+        return false;
       }
       auto& sl = S.slot[s];
+      if (lane < TILES) {
+        sl.cnt[lane] = 0u;
+        sl.sbits[lane] = 0u;
+      }
+      if (lane == 0) sl.base = q * NB;
+      __syncwarp();
+      return true;
+    };
+    auto close_job = [&](bool last) {
+      if (lane == 0) S.slot[s].last = last ? 1 : 0;
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.full[s]);
+      ++k;
+    };
+    uint32_t idx_a, msk_a, idx_b, msk_b;
+    bool val_a, val_b;
+    load_index(chunk_of(0), idx_a, msk_a, val_a);
+    Gathered g_a;
+    gather(idx_a, val_a, g_a);
+    load_index(chunk_of(1), idx_b, msk_b, val_b);
+    for (int u = 0;; ++u) {
+      const int q = chunk_of(u);
+      if (q >= nchunks) break;
+      // the MMA thread stopped: every pixel of the group has finished
+      if (__shfl_sync(0xffffffffu, *stop_flag, 0) != 0) break;
+      Gathered g_b;
+      gather(idx_b, val_b, g_b);  // chunk u + 1
+      uint32_t idx_c, msk_c;
+      bool val_c;
+      load_index(chunk_of(u + 2), idx_c, msk_c, val_c);
+      if (u % kSuper == 0 && !open_job(q)) break;
+      const bool last = u % kSuper == kSuper - 1 || q + 1 >= nchunks;
       const float3 colr = val_a ? make_float3(rgb[3 * idx_a], rgb[3 * idx_a + 1], rgb[3 * idx_a + 2])
                                 : make_float3(0.f, 0.f, 0.f);
       const bool valid = val_a;
@@ -377,19 +449,11 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
       const float2 mu = g_a.mu;
       const float4 co = g_a.co;
       const float lo2 = lg2(co.w);
-      // Cholesky factor of the conic (used for the linear/constant terms and the scalar rows);
-      // here from the hardware reciprocal square root, the determinant by Kahan's scheme
-      float3 Lc = make_float3(0.f, 0.f, 0.f);
-      if (valid) {
-        const float inv = rsqrtf(co.x);
-        const float w2 = co.y * co.y;
-        const float det = fmaf(co.x, co.z, -w2) + fmaf(-co.y, co.y, w2);
-        const float dp = fmaxf(det, 0.f);
-        Lc = make_float3(co.x * inv, co.y * inv, dp > 0.f ? dp * rsqrtf(dp) * inv : 0.f);
-      }
+      // Cholesky factor of the conic (the tile skip and the linear/constant terms)
+      const float3 Lc = valid ? conic_cholesky(co) : make_float3(0.f, 0.f, 0.f);
       const float4 rgbc = make_float4(colr.x, colr.y, colr.z, fminf(lo2, kLog2AlphaMax));
-      sl.sp0[lane] = make_float4(mu.x, mu.y, Lc.x, Lc.y);
-      sl.sp1[lane] = make_float2(Lc.z, lo2);
+      // bit t of `act`: the entry is packed into tile t
+      uint32_t act = 0u;
 #pragma unroll
       for (int t = 0; t < TILES; ++t) {
         const int tx = gx * GW + (t % GW), ty = gy * GH + (t / GW);
@@ -400,77 +464,94 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
           const float qmin = box_min_quadratic(co.x, co.y, co.z, Lc, -mx, 15.f - mx, -my, 15.f - my);
           active = fmaf(-0.5f * kLog2e, qmin, lo2) >= kL255 - kCullMargin;
         }
+        act |= (active ? 1u : 0u) << t;
+      }
+      // a tile whose rows would overflow closes the job; the chunk then starts a new one
+      {
+        bool over = false;
+#pragma unroll
+        for (int t = 0; t < TILES; ++t)
+          over |= S.slot[s].cnt[t] + __popc(__ballot_sync(0xffffffffu, (act >> t) & 1u)) > (uint32_t)NB;
+        if (over) {
+          close_job(false);
+          if (!open_job(q)) break;
+        }
+      }
+      auto& sl = S.slot[s];
+      const uint32_t rel = (uint32_t)(q * NB + lane - sl.base);
+#pragma unroll
+      for (int t = 0; t < TILES; ++t) {
+        const bool active = (act >> t) & 1u;
         const uint32_t bal = __ballot_sync(0xffffffffu, active);
-        const uint32_t cnt_t = __popc(bal);
-        // active entries are packed to rows 0..cnt-1 in list order; the other lanes fill rows
-        // cnt..31 with a row whose exponent never passes the pruning test
-        const uint32_t pos = active ? __popc(bal & lt_mask) : cnt_t + __popc(~bal & lt_mask);
+        if (bal == 0u) continue;
+        const int tx = gx * GW + (t % GW), ty = gy * GH + (t / GW);
+        // active entries are appended to the tile's rows in list order
+        const uint32_t c0 = sl.cnt[t];
+        const uint32_t pos = c0 + __popc(bal & lt_mask);
         bool scalar = false;
-        uint4 r0 = make_uint4(0u, 0u, 0u, 0u), r1 = make_uint4(0u, 0u, 0u, 0u);
-        uint4 r2 = make_uint4(0u, 0u, 0u, 0u);  // BF16: K block 1 (lo)
-        if (!active)  // constant term of the padding rows
-          r0.z = BF ? pack_b2(0.f, -30000.f) : pack_h2(0.f, -30000.f);
         if (active) {
+          uint4 r0 = make_uint4(0u, 0u, 0u, 0u), r1 = make_uint4(0u, 0u, 0u, 0u);
+          uint4 r2 = make_uint4(0u, 0u, 0u, 0u);  // BF16: K block 1 (lo)
           const float mx = mu.x - (float)(tx * kTile + 8), my = mu.y - (float)(ty * kTile + 8);
           // (u, v) = L m: the linear and constant terms are formed from it (conic m = L^T L m and
           // m^T conic m = u^2 + v^2), which avoids the cancellation of the expanded products when
           // the tile is far from the centre of a thin splat
-          const float u = fmaf(Lc.x, mx, Lc.y * my), v = Lc.z * my;
-          float q[6];
-          q[0] = -0.5f * co.x * kLog2e;
-          q[1] = -co.y * kLog2e;
-          q[2] = -0.5f * co.z * kLog2e;
-          q[3] = Lc.x * u * kLog2e;
-          q[4] = fmaf(Lc.y, u, Lc.z * v) * kLog2e;
-          q[5] = fmaf(-0.5f * kLog2e, fmaf(u, u, v * v), lo2);
-          const float wsum = 64.f * (fabsf(q[0]) + fabsf(q[1]) + fabsf(q[2])) +
-                             8.f * (fabsf(q[3]) + fabsf(q[4])) + fabsf(q[5]);
+          const float uu = fmaf(Lc.x, mx, Lc.y * my), vv = Lc.z * my;
+          float qc[6];
+          qc[0] = -0.5f * co.x * kLog2e;
+          qc[1] = -co.y * kLog2e;
+          qc[2] = -0.5f * co.z * kLog2e;
+          qc[3] = Lc.x * uu * kLog2e;
+          qc[4] = fmaf(Lc.y, uu, Lc.z * vv) * kLog2e;
+          qc[5] = fmaf(-0.5f * kLog2e, fmaf(uu, uu, vv * vv), lo2);
+          const float wsum = 64.f * (fabsf(qc[0]) + fabsf(qc[1]) + fabsf(qc[2])) +
+                             8.f * (fabsf(qc[3]) + fabsf(qc[4])) + fabsf(qc[5]);
           scalar = !(wsum <= kMaxWeightedCoef);
           if (!scalar && !BF) {  // FP16: q = hi + lo, residual <= 2^-22 |q|
-            const __half2 h01 = __floats2half2_rn(q[0], q[1]), h23 = __floats2half2_rn(q[2], q[3]),
-                          h45 = __floats2half2_rn(q[4], q[5]);
+            const __half2 h01 = __floats2half2_rn(qc[0], qc[1]),
+                          h23 = __floats2half2_rn(qc[2], qc[3]),
+                          h45 = __floats2half2_rn(qc[4], qc[5]);
             const float2 f01 = __half22float2(h01), f23 = __half22float2(h23),
                          f45 = __half22float2(h45);
             r0.x = *reinterpret_cast<const uint32_t*>(&h01);
             r0.y = *reinterpret_cast<const uint32_t*>(&h23);
             r0.z = *reinterpret_cast<const uint32_t*>(&h45);
-            r0.w = pack_h2(q[0] - f01.x, q[1] - f01.y);
-            r1.x = pack_h2(q[2] - f23.x, q[3] - f23.y);
-            r1.y = pack_h2(q[4] - f45.x, q[5] - f45.y);
+            r0.w = pack_h2(qc[0] - f01.x, qc[1] - f01.y);
+            r1.x = pack_h2(qc[2] - f23.x, qc[3] - f23.y);
+            r1.y = pack_h2(qc[4] - f45.x, qc[5] - f45.y);
           } else if (!scalar) {  // BF16: q = hi + mid + lo, residual <= 2^-27 |q|
             float hi[6], mid[6], lo[6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-              hi[k] = bf16_round(q[k]);
-              mid[k] = bf16_round(q[k] - hi[k]);
-              lo[k] = q[k] - hi[k] - mid[k];
+            for (int kk = 0; kk < 6; ++kk) {
+              hi[kk] = bf16_round(qc[kk]);
+              mid[kk] = bf16_round(qc[kk] - hi[kk]);
+              lo[kk] = qc[kk] - hi[kk] - mid[kk];
             }
             r0 = make_uint4(pack_b2(hi[0], hi[1]), pack_b2(hi[2], hi[3]), pack_b2(hi[4], hi[5]),
                             pack_b2(mid[0], mid[1]));
             r1 = make_uint4(pack_b2(mid[2], mid[3]), pack_b2(mid[4], mid[5]), 0u, 0u);
             r2 = make_uint4(pack_b2(lo[0], lo[1]), pack_b2(lo[2], lo[3]), pack_b2(lo[4], lo[5]), 0u);
           }
+          uint8_t* rowp = &sl.B[t][0][(pos >> 3) * kSBO + (pos & 7) * 16];
+          *reinterpret_cast<uint4*>(rowp) = r0;
+          *reinterpret_cast<uint4*>(rowp + kLBO) = r1;
+          if (KB == 2) {
+            uint8_t* rowq = &sl.B[t][KB - 1][(pos >> 3) * kSBO + (pos & 7) * 16];
+            *reinterpret_cast<uint4*>(rowq) = r2;
+            *reinterpret_cast<uint4*>(rowq + kLBO) = make_uint4(0u, 0u, 0u, 0u);
+          }
           sl.rgbc[t][pos] = rgbc;
-          sl.entry[t][pos] = (uint8_t)lane;
-        }
-        uint8_t* rowp = &sl.B[t][0][(pos >> 3) * kSBO + (pos & 7) * 16];
-        *reinterpret_cast<uint4*>(rowp) = r0;
-        *reinterpret_cast<uint4*>(rowp + kLBO) = r1;
-        if (KB == 2) {
-          uint8_t* rowq = &sl.B[t][KB - 1][(pos >> 3) * kSBO + (pos & 7) * 16];
-          *reinterpret_cast<uint4*>(rowq) = r2;
-          *reinterpret_cast<uint4*>(rowq + kLBO) = make_uint4(0u, 0u, 0u, 0u);
+          sl.rel[t][pos] = (uint16_t)rel;
+          if (scalar) sl.gidx[t][pos] = idx_a;
         }
         const uint32_t sb = __reduce_or_sync(0xffffffffu, (active && scalar) ? (1u << pos) : 0u);
         if (lane == 0) {
-          sl.cnt[t] = cnt_t;
-          sl.sbits[t] = sb;
+          sl.cnt[t] = c0 + (uint32_t)__popc(bal);
+          sl.sbits[t] |= sb;
         }
+        __syncwarp();
       }
-      if (lane == 0) sl.base = c * NB;
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&S.full[s]);
+      if (last) close_job(true);
       // rotate the pipeline
       g_a = g_b;
       idx_a = idx_b;
@@ -486,15 +567,24 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
       constexpr uint32_t idesc = idesc_f16(128, NB, BF);
       int job = 0;
       bool failed = false;
-      for (int c = 0; c < nchunks && !failed; ++c) {
+      // jobs in list order: super-chunk sc comes from producer sc % NPROD, whose jobs for it run
+      // until the one flagged last
+      int kc[NPROD];
+#pragma unroll
+      for (int i = 0; i < NPROD; ++i) kc[i] = 0;
+      const int nsuper = (nchunks + kSuper - 1) / kSuper;
+      int sc = 0;
+      while (sc < nsuper && !failed) {
         // every epilogue warp has finished all its pixels: no more work for this group
         if (*reinterpret_cast<volatile int*>(&S.done_warps) >= C::kEpiWarps) break;
-        const int s = c % SLOTS;
-        if (!mbar_wait_bounded(&S.full[s], (c / SLOTS) & 1, abort_flag, kWaitLimitNs)) {
+        const int pr = sc % NPROD, kk = ring_get(kc, pr);
+        const int s = C::kRing * pr + kk % C::kRing;
+        if (!mbar_wait_bounded(&S.full[s], (kk / C::kRing) & 1, abort_flag, kWaitLimitNs)) {
           failed = true;
           break;
         }
         auto& sl = S.slot[s];
+        const int lastj = sl.last;
         for (int r = 0; r < C::kRounds; ++r, ++job) {
           const int st = job % NST;
           if (!mbar_wait_bounded(&S.tempty[st], ((job / NST) & 1) ^ 1, abort_flag, kWaitLimitNs)) {
@@ -519,6 +609,8 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
           mma_commit(&S.tfull[st]);
         }
         if (!failed) mma_commit(&S.empty[s]);
+        ring_inc(kc, pr);
+        if (lastj) ++sc;
       }
       *stop_flag = 1;
       if (failed) {
@@ -562,8 +654,15 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
     unsigned long long evaluated = 0, passing = 0, slots = 0;
     int job = 0;
     bool finished = false;
-    for (int c = 0; !finished; ++c) {
-      const int s = c % SLOTS;
+    // the MMA thread's job order (super-chunks in turn, each from its producer's ring)
+    int kc[NPROD];
+#pragma unroll
+    for (int i = 0; i < NPROD; ++i) kc[i] = 0;
+    int sc = 0;
+    while (!finished) {
+      const int pr = sc % NPROD, kk = ring_get(kc, pr);
+      const int s = C::kRing * pr + kk % C::kRing;
+      int lastj = 0;
 #pragma unroll
       for (int r = 0; r < C::kRounds; ++r) {
         const int st = job % NST;
@@ -576,8 +675,9 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
         if (r == 0) {
           // the slot's producer writes (colours, packing) are complete: the MMA thread waited on
           // the same phase before issuing this job
-          ok = mbar_wait_bounded(&S.full[s], (c / SLOTS) & 1, abort_flag, kWaitLimitNs);
+          ok = mbar_wait_bounded(&S.full[s], (kk / C::kRing) & 1, abort_flag, kWaitLimitNs);
           if (!__all_sync(0xffffffffu, ok)) { record_abort(&S.abort, err); finished = true; break; }
+          lastj = S.slot[s].last;
         }
         ++job;
         tc_fence_after();
@@ -607,8 +707,8 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
                 if (lane == 0) mbar_arrive(&S.tempty[st]);
               }
               blend_granule<TILES, KB, COUNT, NC, 4>(ga, g, cnt, sb, base, sl, t, tx, ty, quarter,
-                                                     lane, ps[r][0], ps[r][1], evaluated, passing,
-                                                     slots);
+                                                     lane, mean2d, conic_opacity, ps[r][0],
+                                                     ps[r][1], evaluated, passing, slots);
             }
           } else {
             uint32_t ga[16], gb[16];
@@ -627,7 +727,8 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
                 if (lane == 0) mbar_arrive(&S.tempty[st]);
               }
               blend_granule<TILES, KB, COUNT, NC>(ga, g, cnt, sb, base, sl, t, tx, ty, quarter, lane,
-                                          ps[r][0], ps[r][1], evaluated, passing, slots);
+                                                  mean2d, conic_opacity, ps[r][0], ps[r][1],
+                                                  evaluated, passing, slots);
               if (g + 1 < ngr) {
                 tmem_wait_ld(gb);
                 if (g + 2 < ngr) {
@@ -638,8 +739,9 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
                   __syncwarp();
                   if (lane == 0) mbar_arrive(&S.tempty[st]);
                 }
-                blend_granule<TILES, KB, COUNT, NC>(gb, g + 1, cnt, sb, base, sl, t, tx, ty, quarter, lane,
-                                            ps[r][0], ps[r][1], evaluated, passing, slots);
+                blend_granule<TILES, KB, COUNT, NC>(gb, g + 1, cnt, sb, base, sl, t, tx, ty, quarter,
+                                                    lane, mean2d, conic_opacity, ps[r][0], ps[r][1],
+                                                    evaluated, passing, slots);
                 if (g + 2 < ngr) tmem_wait_ld(ga);
               }
             }
@@ -653,6 +755,8 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
         if (r == C::kRounds - 1) {
           __syncwarp();
           if (lane == 0) mbar_arrive(&S.empty[s]);
+          ring_inc(kc, pr);
+          if (lastj) ++sc;
         }
       }
       if (!finished && !counted_done) {
