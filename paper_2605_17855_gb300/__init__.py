@@ -476,7 +476,11 @@ class Renderer:
                      torch.empty((c.height, c.width), device=dev)) for c in self.cameras]
         self.kernels_per_frame = []
         self.g_prep, self.g_raster = [], []
-        self.s_prep = torch.cuda.Stream(device=dev) if self.pipeline else None
+        # The preprocess + bin sort of the next frame runs at the highest stream priority: its chain of
+        # short kernels then takes SM slots as the current frame's raster CTAs retire, instead of
+        # queueing behind the whole raster grid.
+        top = torch.cuda.Stream.priority_range()[1]
+        self.s_prep = torch.cuda.Stream(device=dev, priority=top) if self.pipeline else None
         self.s_raster = torch.cuda.Stream(device=dev) if self.pipeline else None
         self._set_free = [None] * nsets  # event after the last rasterization that read each set
         for k in range(len(self.cameras)):  # run every path once outside capture
