@@ -743,7 +743,8 @@ def main():
            "gpu_launches": launches,
            "kernels_per_frame": rend.kernels_per_frame[0],
            "graphs": "one CUDA graph pair per camera (preprocess + bin sort, rasterize); the preprocess + "
-                     "bin sort of a frame runs on a second stream, overlapping the previous frame's rasterize",
+                     "bin sort of a frame runs on a second stream of the highest priority, overlapping the previous "
+                     "frame's rasterize",
            "clocks": clocks,
            "roofline": roofline}
 

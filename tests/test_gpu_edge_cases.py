@@ -145,3 +145,26 @@ def test_many_groups_use_the_global_count_path():
     assert np.array_equal(_np(bins.vals[:E]).view(np.uint32), ob.vals)
     assert np.array_equal(_np(bins.masks[:E]).view(np.uint16), ob.masks)
     assert np.array_equal(_np(bins.ranges).view(np.uint32), ob.ranges)
+
+
+@pytest.mark.parametrize("tiling", [(1, 1), (2, 2), (4, 4)])
+def test_deep_stack_spans_many_jobs(tiling):
+    # 150 translucent splats over the same tiles: a tile's packed rows overflow the 32 rows of a
+    # tensor-core job several times, so its entries are spread over many jobs (and super-chunks);
+    # the list order, the image and the list positions (n_contrib) must survive the split
+    rng = np.random.default_rng(11)
+    n = 150
+    means = np.stack([rng.uniform(-0.02, 0.02, n), rng.uniform(-0.02, 0.02, n),
+                      np.linspace(2.0, 6.0, n)], 1)
+    scene = _scene(means, np.full((n, 3), 0.5), np.full(n, 0.04), rng.uniform(0, 1, (n, 3)))
+    cam = scenes.identity_camera(96, 80, 60.0)
+    img = _check(scene, cam, tiling)
+    # no pixel terminates (0.96^150 > 1e-4), so central pixels blend every splat
+    assert img.n_contrib[38:42, 46:50].min() == n
+    ds = tgs.DeviceScene.from_host(scene)
+    proj = tgs.preprocess(ds, cam)
+    bins = tgs.bin_sort(proj, cam.width, cam.height, tiling)
+    for prec in ("fp16_tc", "bf16_tc"):
+        _, _, nc = tgs.rasterize(proj, bins, cam.width, cam.height, prec)
+        torch.cuda.synchronize()
+        assert np.array_equal(_np(nc)[38:42, 46:50], img.n_contrib[38:42, 46:50]), prec
