@@ -57,8 +57,10 @@ __device__ void cov2d_f32(const CamParams& c, float3 pc, float4 q, float3 s, flo
 }
 
 // Same quantity in FP64 from the same FP32 inputs (used only for near-degenerate splats).
-__device__ __noinline__ void cov2d_f64(const CamParams& c, const float* m, float4 qf, float3 s, double& cxx,
-                          double& cxy, double& cyy) {
+// Returns (Sxx, Sxy, Syy) by value and takes the mean by value, so that no caller variable has to
+// live in local memory around the call.
+__device__ __noinline__ double3 cov2d_f64(const CamParams& c, float3 mv, float4 qf, float3 s) {
+  const float m[3] = {mv.x, mv.y, mv.z};
   double pc[3];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
@@ -88,9 +90,9 @@ __device__ __noinline__ void cov2d_f64(const CamParams& c, const float* m, float
     T0[col] = (JW[0] * Rq[col] + JW[1] * Rq[3 + col] + JW[2] * Rq[6 + col]) * sv[col];
     T1[col] = (JW[3] * Rq[col] + JW[4] * Rq[3 + col] + JW[5] * Rq[6 + col]) * sv[col];
   }
-  cxx = T0[0] * T0[0] + T0[1] * T0[1] + T0[2] * T0[2];
-  cxy = T0[0] * T1[0] + T0[1] * T1[1] + T0[2] * T1[2];
-  cyy = T1[0] * T1[0] + T1[1] * T1[1] + T1[2] * T1[2];
+  return make_double3(T0[0] * T0[0] + T0[1] * T0[1] + T0[2] * T0[2],
+                      T0[0] * T1[0] + T0[1] * T1[1] + T0[2] * T1[2],
+                      T1[0] * T1[0] + T1[1] * T1[1] + T1[2] * T1[2]);
 }
 
 // Real SH basis up to degree 3 (index l*l + m + l), Condon-Shortley phase kept in the real form.
@@ -157,7 +159,8 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(int n, const float* __res
                                                     const float* __restrict__ scales,
                                                     const float4* __restrict__ quats,
                                                     const float* __restrict__ opac,
-                                                    const float* __restrict__ sh, CamParams c,
+                                                    const float* __restrict__ sh,
+                                                    const __grid_constant__ CamParams c,
                                                     float2* __restrict__ mean2d,
                                                     float4* __restrict__ conic_opacity,
                                                     float* __restrict__ rgb,
@@ -189,8 +192,8 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(int n, const float* __res
     float det = cxx * cyy - cxy * cxy;
     float ca, cb, cc;
     if (!(det >= kDegenerateRatio * cxx * cyy)) {
-      double dxx, dxy, dyy;
-      cov2d_f64(c, m, q, s, dxx, dxy, dyy);
+      const double3 dc = cov2d_f64(c, make_float3(m[0], m[1], m[2]), q, s);
+      double dxx = dc.x, dxy = dc.y, dyy = dc.z;
       dxx += 0.3;
       dyy += 0.3;
       const double ddet = dxx * dyy - dxy * dxy;
