@@ -20,7 +20,8 @@
 //     [hi(6), lo(6), 0, 0, 0, 0] against features [f(6), f(6), 0, 0, 0, 0]: the zero padding of
 //     Section 4.2.3 (exact), with the padding slots used for the lo half. |x|, |y| <= 8, so every
 //     feature is an exact FP16 integer. Rows whose FP16 error bound is too large take a scalar
-//     FP32 path in the epilogue instead. The producers are software-pipelined two chunks deep.
+//     FP32 path in the epilogue instead. A producer's gathers run one chunk ahead of its packing
+//     and its index/mask loads two.
 //     Unless disabled, a producer also leaves out of a tile's packed rows every entry whose exact
 //     maximum exponent over the tile's 16x16 pixel centres is below log2(1/255) by a margin (the
 //     minimum of the conic's quadratic form over a box, in closed form): such an entry fails the
@@ -33,7 +34,8 @@
 //     tcgen05.commit on mbarriers.
 //   * epilogue warpgroups (one per tile of a round): each thread owns one TMEM lane = one pixel in
 //     each of the tile's two 128-pixel M blocks, streams the tile's exponents out of tensor memory
-//     8 columns at a time (the next load in flight while the current columns are blended) and runs
+//     8 columns at a time with the next load in flight (4 at a time, single-buffered, in the
+//     one-stage configurations, whose register budget is 48 per thread) and runs
 //     the front-to-back blend of Section 2 in FP32: skip if alpha < 1/255 (tested in the log2
 //     domain before the exp), alpha = min(0.99, 2^D), stop when T' < 1e-4 without blending.
 // Each chunk is loaded from global memory once per group and reused by all member tiles
