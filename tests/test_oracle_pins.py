@@ -116,6 +116,42 @@ def _mc_projected_cov(mean, scale, quat_wxyz, cam, n=2_000_000, seed=0):
     return np.cov(np.stack([u, v]))
 
 
+def _with_focal(cam, fx, fy):
+    """The camera with its focal lengths replaced (fx != fy exercises the two axes separately)."""
+    import dataclasses
+    return dataclasses.replace(cam, fx=float(np.float32(fx)), fy=float(np.float32(fy)))
+
+
+@pytest.mark.parametrize("cam_kind", ["identity", "look_at"])
+def test_projection_off_axis_from_back_projection(orc, cam_kind):
+    # The inverse route: start from a pixel (u, v) and a depth z, walk from the camera centre along
+    # its right / down / forward axes by ((u - cx) z / fx, (v - cy) z / fy, z), and put a splat
+    # there. Its projected mean must land back on (u, v) and its depth must be z. x != y, fx != fy
+    # and an off-centre principal point (W != H) make a swapped axis or focal length visible.
+    if cam_kind == "identity":
+        cam = _with_focal(scenes.identity_camera(240, 130), 150.0, 95.0)
+        eye = np.zeros(3)
+        right, down, fwd = np.eye(3)
+    else:
+        base = scenes.look_at_camera([2.0, 1.0, -3.0], [0.0, 0.2, 0.0], 200, 150)
+        cam = _with_focal(base, 180.0, 120.0)
+        eye = np.asarray(base.cam_pos, np.float64)
+        fwd = np.array([0.0, 0.2, 0.0]) - np.array([2.0, 1.0, -3.0])
+        fwd /= np.linalg.norm(fwd)
+        down = -(np.array([0.0, 1.0, 0.0]) - fwd[1] * fwd)
+        down /= np.linalg.norm(down)
+        right = np.cross(down, fwd)
+    for (u, v, z) in ((37.25, 101.5, 2.5), (cam.width - 20.75, 12.125, 4.0), (150.5, 20.0, 1.7)):
+        X = (u - cam.cx) * z / cam.fx
+        Y = (v - cam.cy) * z / cam.fy
+        p = eye + X * right + Y * down + z * fwd
+        pr = orc.preprocess(_single(p, [0.01] * 3, [1, 0, 0, 0]), cam)
+        assert pr.radius[0] > 0
+        # float32 rounding of the world-space mean moves the projection by ~1e-4 px
+        np.testing.assert_allclose(pr.mean2d[0], [u, v], atol=2e-3)
+        assert pr.depth[0] == pytest.approx(z, rel=1e-5)
+
+
 @pytest.mark.parametrize("cam_kind", ["identity", "look_at"])
 def test_ewa_covariance_matches_monte_carlo(orc, cam_kind):
     if cam_kind == "identity":
@@ -413,7 +449,41 @@ def test_pixel_list_matches_full_frame(orc):
 # ------------------------------------------------------------------------------------------------
 # Backward of the blend: analytic chain rule vs FP64 central differences of the forward.
 
-def test_backward_matches_central_differences(orc):
+def _fd_check(orc, W, H, mu, conic, opac, rgb, depth, pix, G, bg=(0.0, 0.0, 0.0), radius=16,
+              tiling=(2, 2)):
+    """Analytic gradient of L = sum(image[pix] * G) against FP64 central differences of the
+    forward. Returns the analytic gradients."""
+    b = _bins_for(orc, mu, [radius] * len(opac), depth, W, H, *tiling)
+
+    def loss(m, cn, o, c):
+        img = orc.blend(W, H, m, cn, o, c, b, bg=bg, pixels=pix)
+        return float(np.sum(img.rgb * G)), img
+
+    _, base = loss(mu, conic, opac, rgb)
+    assert base.margin.min() > 1e-3  # FD steps stay on one side of every threshold
+    g = orc.blend_backward(W, H, mu, conic, opac, rgb, b, G, bg=bg, pixels=pix)
+    names = ["mean2d", "conic", "opacity", "rgb"]
+    for name, arr, grad in (("mean2d", mu, g.mean2d), ("conic", conic, g.conic),
+                            ("opacity", opac, g.opacity), ("rgb", rgb, g.rgb)):
+        flat = arr.reshape(-1)
+        fd = np.zeros_like(flat)
+        for k in range(flat.size):
+            h = 1e-6 * max(1.0, abs(flat[k]))
+            args = [mu.copy(), conic.copy(), opac.copy(), rgb.copy()]
+            idx = names.index(name)
+            args[idx].reshape(-1)[k] += h
+            lp, _ = loss(*args)
+            args[idx].reshape(-1)[k] -= 2 * h
+            lm, _ = loss(*args)
+            fd[k] = (lp - lm) / (2 * h)
+        np.testing.assert_allclose(grad.reshape(-1), fd, rtol=1e-5, atol=1e-7 * max(np.abs(fd).max(), 1e-3),
+                                   err_msg=name)
+    return g, base
+
+
+@pytest.mark.parametrize("bg", [(0.0, 0.0, 0.0), (0.3, 0.6, 0.9)])
+def test_backward_matches_central_differences(orc, bg):
+    # a random stack; with a non-zero background the colour behind each entry includes bg T_final
     rng = np.random.default_rng(7)
     W, H, n = 32, 32, 12
     mu = np.stack([rng.uniform(6, 26, n), rng.uniform(6, 26, n)], 1)
@@ -422,29 +492,54 @@ def test_backward_matches_central_differences(orc):
     opac = rng.uniform(0.2, 0.7, n)
     rgb = rng.uniform(0, 1, (n, 3))
     depth = rng.uniform(1, 3, n)
-    b = _bins_for(orc, mu, [16] * n, depth, W, H, 2, 2)
     pix = np.array([(x, y) for y in range(10, 22, 2) for x in range(10, 22, 2)])
     G = rng.standard_normal((len(pix), 3))
+    g, base = _fd_check(orc, W, H, mu, conic, opac, rgb, depth, pix, G, bg)
+    if any(bg):  # the background term is live: T_final < 1 at the pixels and non-zero gradients
+        assert base.T.max() < 1.0 and np.abs(g.opacity).max() > 0
 
-    def loss(m, cn, o, c):
-        img = orc.blend(W, H, m, cn, o, c, b, pixels=pix)
-        return float(np.sum(img.rgb * G)), img
 
-    _, base = loss(mu, conic, opac, rgb)
-    assert base.margin.min() > 1e-3  # FD steps stay on one side of every threshold
-    g = orc.blend_backward(W, H, mu, conic, opac, rgb, b, G, pixels=pix)
-    for name, arr, grad in (("mean2d", mu, g.mean2d), ("conic", conic, g.conic),
-                            ("opacity", opac, g.opacity), ("rgb", rgb, g.rgb)):
-        flat = arr.reshape(-1)
-        fd = np.zeros_like(flat)
-        for k in range(flat.size):
-            h = 1e-6 * max(1.0, abs(flat[k]))
-            args = [mu.copy(), conic.copy(), opac.copy(), rgb.copy()]
-            idx = ["mean2d", "conic", "opacity", "rgb"].index(name)
-            args[idx].reshape(-1)[k] += h
-            lp, _ = loss(*args)
-            args[idx].reshape(-1)[k] -= 2 * h
-            lm, _ = loss(*args)
-            fd[k] = (lp - lm) / (2 * h)
-        np.testing.assert_allclose(grad.reshape(-1), fd, rtol=1e-5, atol=1e-7 * np.abs(fd).max(),
-                                   err_msg=name)
+def test_backward_alpha_cap_passes_no_gradient(orc):
+    # Splat 1 reaches o e^power > 0.99 at the test pixel: its alpha is the constant 0.99 there, so
+    # neither its opacity nor its power inputs (mean, conic) receive a gradient from that pixel;
+    # its colour still does. Splats 0 (in front) and 2 (behind) are below the cap.
+    W = H = 32
+    mu = np.array([[11.0, 8.5], [10.1, 9.85], [12.0, 11.0]])
+    conic = np.array([[0.08, 0.01, 0.1], [1 / 9, 0.0, 1 / 9], [0.05, -0.01, 0.06]])
+    opac = np.array([0.4, 0.998, 0.7])
+    rgb = np.array([[0.9, 0.1, 0.2], [0.3, 0.8, 0.4], [0.2, 0.3, 0.95]])
+    depth = np.array([1.0, 2.0, 3.0])
+    pix = np.array([(10, 10)])
+    d = pix[0] - mu[1]
+    oe = opac[1] * math.exp(-0.5 * (conic[1, 0] * d[0] ** 2 + conic[1, 2] * d[1] ** 2)
+                            - conic[1, 1] * d[0] * d[1])
+    assert oe - 0.99 > 1e-3  # the cap holds on both sides of every FD step
+    G = np.array([[0.7, -1.1, 0.4]])
+    g, base = _fd_check(orc, W, H, mu, conic, opac, rgb, depth, pix, G, bg=(0.1, 0.2, 0.3))
+    assert g.opacity[1] == 0.0 and np.all(g.conic[1] == 0.0) and np.all(g.mean2d[1] == 0.0)
+    assert np.all(g.rgb[1] != 0.0)
+    assert g.opacity[0] != 0.0 and g.opacity[2] != 0.0
+
+
+def test_backward_early_termination(orc):
+    # Four nearly opaque splats and a faint one over the test pixels: T falls 1 -> ~0.05 -> ~2.5e-3 -> ~1.3e-4,
+    # the fourth would take it below 1e-4 and ends the pixel unblended. The fourth and fifth
+    # splats therefore get no gradient at all (their parameters do not change the image), and the
+    # first three get the gradient of a stack that stops there.
+    W = H = 32
+    n = 5
+    mu = np.array([[16.2, 15.9], [15.8, 16.1], [16.1, 16.3], [15.9, 15.7], [16.3, 16.2]])
+    conic = np.tile([[0.02, 0.002, 0.025]], (n, 1))
+    opac = np.array([0.96, 0.95, 0.95, 0.97, 0.1])  # a faint fifth splat would still blend
+    rgb = np.random.default_rng(5).uniform(0.1, 0.9, (n, 3))
+    depth = np.arange(1.0, n + 1.0)
+    pix = np.array([(16, 16), (17, 15), (15, 17)])
+    G = np.random.default_rng(6).standard_normal((len(pix), 3))
+    g, base = _fd_check(orc, W, H, mu, conic, opac, rgb, depth, pix, G, bg=(0.5, 0.25, 0.75))
+    assert np.all(base.n_contrib == 3)
+    assert np.all(base.T < 1e-3) and np.all(base.T >= 1e-4)
+    assert base.evaluated == 4 * len(pix)  # the fourth splat is evaluated and stops the pixel
+    for k in (3, 4):
+        assert g.opacity[k] == 0.0 and np.all(g.conic[k] == 0.0) and np.all(g.mean2d[k] == 0.0)
+        assert np.all(g.rgb[k] == 0.0)
+    assert np.all(g.opacity[:3] != 0.0)
