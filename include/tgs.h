@@ -22,9 +22,12 @@
  *   - Device pointers are caller-owned, contiguous, row-major. Floating point is FP32 unless stated.
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream). All work is enqueued on it;
  *     no call synchronizes the stream unless its comment says so.
- *   - The library allocates device memory only inside objects it creates (tgs_server), plus one
- *     4-byte device error word per device on first use. The bin sort takes a caller-provided
- *     workspace sized by tgs_bin_sort_workspace_size.
+ *   - The library allocates device memory only inside objects it creates (tgs_server). Its
+ *     device error word (one int32 per device) is a variable of the library's own device code,
+ *     not an allocation. The bin sort takes a caller-provided workspace sized by
+ *     tgs_bin_sort_workspace_size.
+ *   - The library caches per-device state (the error word's address, the static scratch's
+ *     address) for the life of the process: do not use it again after cudaDeviceReset.
  *   - The image is sampled at integer pixel coordinates: pixel (i, j) is at (x, y) = (i, j).
  *     Tiles are 16x16 pixels. A tile group is group_w x group_h tiles (1x1 up to 4x4).
  */
@@ -164,12 +167,16 @@ tgs_status tgs_bin_sort(const tgs_projected* proj, int64_t n, int32_t width, int
  * counterpart: this serves callers that cannot allocate device memory while they run (a real-time
  * frame loop or compositor with a memory budget fixed at start-up, or a host application that owns
  * every device allocation). The scratch is a fixed TGS_BIN_SORT_STATIC_BYTES array inside the
- * library, held by every GPU that loads it until the process exits. Same arguments, outputs and
- * errors as tgs_bin_sort, plus TGS_ERR_CAPACITY (with a message) when
+ * library, held by every GPU that loads it until the process exits. No call, the first one
+ * included, allocates device memory. Same arguments, outputs and errors as tgs_bin_sort, plus
+ * TGS_ERR_CAPACITY with *num_entries_host = -1 (if given) and a message when
  * tgs_bin_sort_workspace_size(n, bins->capacity, ...) exceeds TGS_BIN_SORT_STATIC_BYTES (e.g.
- * about 130k Gaussians with 1M entries). The first call on a device resolves the array's device
- * address (cudaGetSymbolAddress) and must come before any stream capture on that device. All
- * calls share the array; calls that overlap on the GPU (other streams or host threads) race. */
+ * about 130k Gaussians with 1M entries); the TGS_ERR_CAPACITY of a frame that needs more entries
+ * than bins->capacity leaves the needed count (>= 0) there instead. The first call on a device
+ * loads the library's device code on that device (CUDA loads modules lazily), which commits the
+ * array's memory, and resolves its address (cudaGetSymbolAddress): make that first call at
+ * start-up, before any stream capture on that device. All calls share the array; calls that
+ * overlap on the GPU (other streams or host threads) race. */
 tgs_status tgs_bin_sort_static(const tgs_projected* proj, int64_t n, int32_t width, int32_t height,
                                const tgs_tiling* tiling, tgs_bins* bins, int64_t* num_entries_host,
                                void* stream);
@@ -197,7 +204,8 @@ tgs_status tgs_rasterize(const tgs_projected* proj, int64_t n, const tgs_bins* b
  * from n_contrib, recovering T_i = T_{i+1} / (1 - alpha_i) from the stored final T. Outputs are
  * overwritten (the call zeroes them first): g_mean2d [n,2] (d/d mu' in pixels), g_conic_opacity
  * [n,4] (d/da, d/db, d/dc, d/do), g_rgb [n,3]. Inputs are those of the forward call plus its
- * out_T and n_contrib. FP32 arithmetic; the forward must have been run in the same precision. */
+ * out_T and n_contrib. FP32 arithmetic: the forward must have been an FP32 call
+ * (opts->precision == TGS_PRECISION_FP32, else TGS_ERR_INVALID_ARGUMENT). */
 tgs_status tgs_rasterize_backward(const tgs_projected* proj, int64_t n, const tgs_bins* bins,
                                   int32_t width, int32_t height, const tgs_tiling* tiling,
                                   const tgs_raster_opts* opts, const float* out_T,
@@ -208,6 +216,11 @@ tgs_status tgs_rasterize_backward(const tgs_projected* proj, int64_t n, const tg
 /* Number of CUDA kernels this library has launched in this process (all devices, all threads).
  * A diagnostic for counting the kernels of a timed region. */
 int64_t tgs_kernel_launch_count(void);
+
+/* Number of memory allocations (device memory, and pinned host memory) this library has made in
+ * this process: only tgs_serve_* objects allocate. A diagnostic for callers that must not
+ * allocate. */
+int64_t tgs_allocation_count(void);
 
 /* Device-side error word of the library on the current device (TGS_OK or TGS_ERR_TIMEOUT), set by
  * a kernel whose bounded wait expired. Synchronizes the device. reset != 0 clears it. */

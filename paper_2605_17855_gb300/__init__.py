@@ -124,6 +124,7 @@ SIGNATURES = {
                                            _P, _P, _P, _P, _P]),
     "tgs_last_device_error": (C.c_int32, [C.c_int32]),
     "tgs_kernel_launch_count": (C.c_int64, []),
+    "tgs_allocation_count": (C.c_int64, []),
     "tgs_serve_create": (C.c_int32, [C.POINTER(_ServeConfig), C.POINTER(_P)]),
     "tgs_serve_add_scene": (C.c_int32, [_P, C.POINTER(_Scene), C.POINTER(C.c_int32)]),
     "tgs_serve_remove_scene": (C.c_int32, [_P, C.c_int32]),

@@ -12,8 +12,19 @@ namespace tgs {
 
 static thread_local char g_msg[512] = "";
 static std::atomic<int64_t> g_launches{0};
+static std::atomic<int64_t> g_allocations{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Every allocation of the library goes through these two (counted by tgs_allocation_count).
+cudaError_t device_malloc(void** p, size_t bytes) {
+  g_allocations.fetch_add(1, std::memory_order_relaxed);
+  return cudaMalloc(p, bytes);
+}
+cudaError_t pinned_malloc(void** p, size_t bytes) {
+  g_allocations.fetch_add(1, std::memory_order_relaxed);
+  return cudaMallocHost(p, bytes);
+}
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -27,7 +38,13 @@ tgs_status cuda_status(cudaError_t e, const char* what) {
   return TGS_ERR_CUDA;
 }
 
-// One zero-initialized int32 per device, allocated on first use and kept for the process.
+// The device-side error word: a zero-initialized int32 in this library's own device memory, one
+// per device (a file-scope __device__ variable, so no call ever allocates it). Kernels receive its
+// device address as an argument; the address is looked up once per device with
+// cudaGetSymbolAddress and cached. The cache assumes the device's context lives as long as the
+// process: after cudaDeviceReset the library must not be used again in that process.
+static __device__ int32_t g_device_error = 0;
+
 int32_t* device_error_word() {
   static std::mutex mu;
   static int32_t* words[64] = {nullptr};
@@ -35,10 +52,9 @@ int32_t* device_error_word() {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
   std::lock_guard<std::mutex> lock(mu);
   if (!words[dev]) {
-    int32_t* p = nullptr;
-    if (cudaMalloc(&p, sizeof(int32_t)) != cudaSuccess) return nullptr;
-    if (cudaMemset(p, 0, sizeof(int32_t)) != cudaSuccess) return nullptr;
-    words[dev] = p;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_device_error) != cudaSuccess) return nullptr;
+    words[dev] = static_cast<int32_t*>(p);
   }
   return words[dev];
 }
@@ -99,6 +115,8 @@ const char* tgs_last_error_message(void) { return g_msg; }
 int32_t tgs_abi_version(void) { return TGS_ABI_VERSION; }
 
 int64_t tgs_kernel_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int64_t tgs_allocation_count(void) { return g_allocations.load(std::memory_order_relaxed); }
 
 tgs_status tgs_check_device(int32_t device) { return require_sm103(device); }
 
@@ -212,6 +230,12 @@ tgs_status tgs_rasterize_backward(const tgs_projected* proj, int64_t n, const tg
   g_msg[0] = 0;
   tgs_status s = check_raster_args(proj, n, bins, width, height, tiling, opts);
   if (s != TGS_OK) return s;
+  // the backward replays the FP32 forward's decisions: outputs of another precision's forward
+  // would give the gradient of a different image
+  if (opts->precision != TGS_PRECISION_FP32)
+    return set_error("the backward needs the outputs of an FP32 forward (precision %d given)",
+                     opts->precision),
+           TGS_ERR_INVALID_ARGUMENT;
   if (!out_T || !n_contrib || !grad_rgb || (n > 0 && (!g_mean2d || !g_conic_opacity || !g_rgb)))
     return set_error("null argument"), TGS_ERR_INVALID_ARGUMENT;
   s = require_current_sm103();

@@ -7,12 +7,15 @@
 // the library as a file-scope __device__ array. Every GPU that loads the library holds that area
 // until the process exits, so its size is kept modest (TGS_BIN_SORT_STATIC_BYTES).
 //
-// It allocates nothing: no cudaMalloc, cudaFree or allocating library call. On its first call on a
-// device (with that device current) it looks up the device address of the array with
-// cudaGetSymbolAddress and caches it; that first call should therefore come before any stream
-// capture. All calls share the one array and it keeps the last call's contents; the bin sort
-// writes every scratch word it reads, so nothing needs clearing, but calls whose work overlaps on
-// the GPU (different streams, or different host threads on the same device) race on the array.
+// It allocates nothing, on its first call as on every other: no cudaMalloc, cudaFree or allocating
+// library call (the library's device error word is a __device__ variable too). On its first call
+// on a device (with that device current) it looks up the device address of the array with
+// cudaGetSymbolAddress and caches it. CUDA loads a library's device code lazily, so that first
+// call is also when the array's memory is committed on the device: a caller with a memory budget
+// fixed at start-up should make it then, before any stream capture. All calls share the one array
+// and it keeps the last call's contents; the bin sort writes every scratch word it reads (and
+// clears its counters itself), so nothing needs clearing, but calls whose work overlaps on the GPU
+// (different streams, or different host threads on the same device) race on the array.
 #include <mutex>
 
 #include "tgs_internal.cuh"
@@ -39,6 +42,12 @@ tgs_status scratch_address(void** out) {
   if (!g_scratch[dev]) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_bin_sort_scratch);
+    if (e == cudaErrorMemoryAllocation) {
+      tgs::set_error("loading the %zu-byte static bin-sort scratch on device %d failed: out of "
+                     "device memory (make the first tgs_bin_sort_static call at start-up)",
+                     kStaticScratchBytes, dev);
+      return TGS_ERR_CUDA;
+    }
     if (e != cudaSuccess) return tgs::cuda_status(e, "cudaGetSymbolAddress(bin sort scratch)");
     g_scratch[dev] = p;
   }
@@ -63,6 +72,7 @@ extern "C" tgs_status tgs_bin_sort_static(const tgs_projected* proj, int64_t n, 
         "tgs_bin_sort_static: %lld Gaussians with capacity %lld need %zu bytes of scratch; the "
         "static area holds %zu bytes (use tgs_bin_sort with a caller workspace)",
         (long long)n, (long long)bins->capacity, need, kStaticScratchBytes);
+    if (num_entries_host) *num_entries_host = -1;  // not a frame's entry count
     return TGS_ERR_CAPACITY;
   }
   void* ws = nullptr;

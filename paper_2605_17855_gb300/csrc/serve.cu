@@ -145,7 +145,7 @@ tgs_status ensure_buffers(tgs_server* S, Slot& sl, int64_t n, int64_t cap, const
     lost = true;
     S->unreserve(old_bytes);
     sl.bytes -= old_bytes;
-    const cudaError_t e = cudaMalloc(mem, new_bytes);
+    const cudaError_t e = device_malloc(mem, new_bytes);
     if (e != cudaSuccess) {
       S->unreserve(new_bytes);
       return cuda_status(e, "cudaMalloc (serving slot)");
@@ -383,7 +383,7 @@ tgs_status tgs_serve_create(const tgs_serve_config* config, tgs_server** out) {
   for (Slot& sl : S->slots) {
     cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&sl.host), sizeof(Readback));
+    if (e == cudaSuccess) e = pinned_malloc(reinterpret_cast<void**>(&sl.host), sizeof(Readback));
     if (e != cudaSuccess) {
       for (Slot& t : S->slots) {
         if (t.stream) cudaStreamDestroy(t.stream);
@@ -418,7 +418,7 @@ tgs_status tgs_serve_add_scene(tgs_server* S, const tgs_scene* scene, int32_t* s
   DeviceGuard guard(S->cfg.device);
   TGS_CUDA(guard.status);
   SceneRec rec;
-  cudaError_t e = cudaMalloc(&rec.mem, bytes);
+  cudaError_t e = device_malloc(&rec.mem, bytes);
   if (e != cudaSuccess) {
     S->unreserve(bytes);
     return cuda_status(e, "cudaMalloc (scene)");

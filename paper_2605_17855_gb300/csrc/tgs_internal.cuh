@@ -14,7 +14,8 @@ namespace tgs {
 // Host-side error plumbing (implemented in abi.cu).
 void set_error(const char* fmt, ...);
 tgs_status cuda_status(cudaError_t e, const char* what);
-// Device-side error word of the current device (allocated once per device, zero-initialized).
+// Device-side error word of the current device: a zero-initialized __device__ variable of the
+// library (nothing is allocated); its address is looked up once per device.
 int32_t* device_error_word();
 
 #define TGS_CUDA(expr)                                              \
@@ -24,6 +25,10 @@ int32_t* device_error_word();
   } while (0)
 
 void note_launch();  // counts kernel launches (tgs_kernel_launch_count)
+// The library's only ways to allocate memory (device, and pinned host); both are counted
+// (tgs_allocation_count).
+cudaError_t device_malloc(void** p, size_t bytes);
+cudaError_t pinned_malloc(void** p, size_t bytes);
 
 #define TGS_CHECK_LAUNCH(what)                                      \
   do {                                                              \

@@ -142,3 +142,36 @@ def test_size_limits_are_checked_on_the_host(lib):
     # image sizes up to 16384 per side
     assert lib.tgs_bin_sort_workspace_size(10, 10, 16385, 64, C.byref(t), C.byref(out)) == 1
     assert lib.tgs_bin_sort_workspace_size(10, 10, 16384, 16384, C.byref(t), C.byref(out)) == 0
+
+
+def test_backward_rejects_a_tensor_core_forward(lib):
+    # the backward replays the FP32 forward's decisions; a tensor-core forward's outputs would give
+    # the gradient of a different image, so the ABI refuses any other precision before device work
+    import ctypes as C
+
+    import paper_2605_17855_gb300 as tgs
+    proj = tgs._Projected()
+    b = tgs._Bins()
+    b.ranges = C.c_void_p(256)  # never dereferenced: the call stops at argument validation
+    t = tgs._Tiling(2, 2)
+    dummy = C.c_void_p(256)
+    for prec in (tgs.PRECISION["fp16_tc"], tgs.PRECISION["bf16_tc"], 7):
+        o = tgs._RasterOpts(prec, 0, (C.c_float * 3)(0, 0, 0), None)
+        st = lib.tgs_rasterize_backward(C.byref(proj), 0, C.byref(b), 64, 64, C.byref(t), C.byref(o),
+                                        dummy, dummy, dummy, None, None, None, None)
+        assert st == tgs.TGS_ERR_INVALID_ARGUMENT
+        assert b"FP32 forward" in lib.tgs_last_error_message()
+
+
+def test_every_allocation_goes_through_the_counted_helpers():
+    # tgs_allocation_count is only meaningful if no source allocates around it
+    pat = re.compile(r"\bcuda(Malloc|MallocHost|MallocManaged|MallocAsync|HostAlloc|MallocPitch|"
+                     r"Malloc3D|MallocArray)\s*\(")
+    for p in glob.glob(os.path.join(ROOT, "paper_2605_17855_gb300", "csrc", "*")):
+        src = re.sub(r"//[^\n]*", "", re.sub(r"/\*.*?\*/", "", open(p).read(), flags=re.S))
+        src = re.sub(r'"(?:[^"\\\n]|\\.)*"', '""', src)  # string literals (error messages)
+        hits = pat.findall(src)
+        if os.path.basename(p) == "abi.cu":
+            assert sorted(hits) == ["Malloc", "MallocHost"], hits  # the two helpers themselves
+        else:
+            assert not hits, (p, hits)

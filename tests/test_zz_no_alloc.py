@@ -6,6 +6,10 @@ workspace version's exactly (binning is integer work), on two calls in a row tha
 This file is collected last on purpose: if it fails, a run that stops at the first failure has
 already run every other test. It does not depend on any other test's state."""
 import ctypes as C
+import json
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -82,7 +86,31 @@ def test_static_scratch_rejects_oversized_requests(n, capacity, width, height, t
     lib = tgs.load()
     big = tgs.allocate_bins(n, capacity, cam.width, cam.height, tiling)
     t = tgs._Tiling(*tiling)
+    host = C.c_int64(123)
     st = lib.tgs_bin_sort_static(C.byref(proj.struct()), n, cam.width, cam.height, C.byref(t),
-                                 C.byref(big.struct()), None, None)
+                                 C.byref(big.struct()), C.byref(host), None)
     assert st == tgs.TGS_ERR_CAPACITY
     assert b"static area holds" in lib.tgs_last_error_message()
+    assert host.value == -1  # not an entry count: a caller must not retry with a larger capacity
+
+
+def test_first_call_in_a_fresh_process_allocates_nothing():
+    # A process whose very first library call is tgs_bin_sort_static: the library makes no
+    # allocation at all (its counter of cudaMalloc / cudaMallocHost calls stays 0), the bins equal
+    # the oracle's on three calls in a row, and device memory does not move across the later
+    # calls. The first call may commit the library's device code and the static array (CUDA loads
+    # modules lazily), which is bounded by the array's size plus the code.
+    tgs.load()  # built before the child starts
+    child = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_static_first_call.py")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, child, root], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    assert res["allocation_count"] == 0
+    for c in res["calls"]:
+        assert c["status"] == tgs.TGS_OK, c["message"]
+        assert c["entries"] == c["oracle_entries"] > 0 and c["equal"]
+    first, *later = res["calls"]
+    assert 0 <= first["free_before"] - first["free_after"] <= (16 << 20) + (48 << 20)
+    for c in later:
+        assert c["free_before"] == c["free_after"]
