@@ -62,10 +62,11 @@ def _load():
             lib.orc_project_cov.argtypes = [_P, _P, _P, C.POINTER(OrcCamera), _P]
             lib.orc_tile_rect.argtypes = [C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_int32, _P]
             lib.orc_tile_rect.restype = C.c_int32
-            lib.orc_bin_count.argtypes = [C.c_int64, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+            lib.orc_bin_count.argtypes = [C.c_int64, _P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32,
+                                          C.c_int32]
             lib.orc_bin_count.restype = C.c_int64
-            lib.orc_bin.argtypes = [C.c_int64, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
-                                    _P, _P, _P, _P]
+            lib.orc_bin.argtypes = [C.c_int64, _P, _P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32,
+                                    C.c_int32, _P, _P, _P, _P]
             lib.orc_blend.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, _P, _P, _P,
                                       _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P]
             lib.orc_blend_backward.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
@@ -172,21 +173,30 @@ class Bins:
         return int(self.keys.shape[0])
 
 
-def bin_sort(mean2d, radius, depth, width, height, gw=2, gh=2) -> Bins:
+def bin_sort(mean2d, radius, depth, width, height, gw=2, gh=2, conic=None, opacity=None) -> Bins:
     """Group entries + masks, sorted by (group, depth, index). Takes the projected mean, radius and
-    depth of either side (float32 inputs are widened exactly)."""
+    depth of either side (float32 inputs are widened exactly). With conic [n,3] and opacity [n]
+    (float32 values) a tile of a splat's range is kept only if the splat can reach alpha >= 1/255
+    in it (the membership test, taken in FP32 as the kernels take it); without them every tile of
+    the range is kept."""
     lib = _load()
     mean2d, depth = _f64(mean2d).reshape(-1, 2), _f64(depth).reshape(-1)
     radius = np.ascontiguousarray(radius, np.int32).reshape(-1)
     n = radius.shape[0]
-    E = int(lib.orc_bin_count(n, _ptr(mean2d), _ptr(radius), width, height, gw, gh))
+    if (conic is None) != (opacity is None):
+        raise ValueError("conic and opacity go together")
+    if conic is not None:
+        conic = _f64(np.asarray(conic, np.float32)).reshape(n, 3)
+        opacity = _f64(np.asarray(opacity, np.float32)).reshape(n)
+    E = int(lib.orc_bin_count(n, _ptr(mean2d), _ptr(radius), _ptr(conic), _ptr(opacity), width, height,
+                              gw, gh))
     _, _, GX, GY = group_grid(width, height, gw, gh)
     keys = np.zeros(max(E, 1), np.uint64)
     vals = np.zeros(max(E, 1), np.uint32)
     masks = np.zeros(max(E, 1), np.uint16)
     ranges = np.zeros((GX * GY, 2), np.uint32)
-    lib.orc_bin(n, _ptr(mean2d), _ptr(radius), _ptr(depth), width, height, gw, gh, _ptr(keys),
-                _ptr(vals), _ptr(masks), _ptr(ranges))
+    lib.orc_bin(n, _ptr(mean2d), _ptr(radius), _ptr(depth), _ptr(conic), _ptr(opacity), width, height,
+                gw, gh, _ptr(keys), _ptr(vals), _ptr(masks), _ptr(ranges))
     return Bins(keys[:E], vals[:E], masks[:E], ranges, gw, gh)
 
 
@@ -254,10 +264,11 @@ def blend_backward(width, height, mean2d, conic, opacity, rgb, bins: Bins, grad_
     return out
 
 
-def render(scene, cam, gw=2, gh=2, bg=(0.0, 0.0, 0.0)):
+def render(scene, cam, gw=2, gh=2, bg=(0.0, 0.0, 0.0), membership=True):
     """Full oracle frame: preprocess -> bin/sort -> blend. Returns (Projected, Bins, Image)."""
     pr = preprocess(scene, cam)
-    bins = bin_sort(pr.mean2d, pr.radius, pr.depth, cam.width, cam.height, gw, gh)
+    extra = dict(conic=pr.conic, opacity=pr.opacity) if membership else {}
+    bins = bin_sort(pr.mean2d, pr.radius, pr.depth, cam.width, cam.height, gw, gh, **extra)
     img = blend(cam.width, cam.height, pr.mean2d, pr.conic, pr.opacity, pr.rgb, bins, bg)
     return pr, bins, img
 

@@ -27,6 +27,12 @@
  *     image pixels lies inside it (closed bounds);
  *   - SH: real spherical harmonics, degree <= 3, index l*l + m + l, Condon-Shortley phase kept in the
  *     real form; colour = sum + 0.5, clamped at 0 per channel;
+ *   - tile membership (beyond the paper, whose Section 6 cites tighter splat footprints): a tile of
+ *     the AABB's range stays in a splat's entry only if the splat's ellipse at the level where
+ *     o e^power could reach 1/255 (plus slack) meets the tile's pixel-centre box; the test is a
+ *     decision about which entries exist, so it is taken in FP32 with a fixed operation order
+ *     (member_setup / member_row below), the precision of the kernels, and it is conservative:
+ *     a dropped (splat, tile) pair is pruned at every pixel of the tile;
  *   - group IDs are row-major over groups; mask bit (ty - gy*gh)*gw + (tx - gx*gw);
  *     key = (gid << 32) | bits(float(depth)), ties broken by splat index;
  *   - alpha = min(0.99, o exp(power)); alpha < 1/255 skips; an entry whose T' = T (1 - alpha)
@@ -252,21 +258,135 @@ static void group_grid(int32_t width, int32_t height, int32_t gw, int32_t gh, in
   *GY = (*TY + gh - 1) / gh;
 }
 
-int64_t orc_bin_count(int64_t n, const double* mean2d, const int32_t* radius, int32_t width,
-                      int32_t height, int32_t gw, int32_t gh) {
-  int64_t total = 0;
-  for (int64_t i = 0; i < n; ++i) {
-    if (radius[i] <= 0) continue;
-    int32_t rc[4];
-    if (!orc_tile_rect(mean2d[2 * i], mean2d[2 * i + 1], radius[i], width, height, rc)) continue;
-    const int64_t gx0 = rc[0] / gw, gx1 = (rc[2] - 1) / gw + 1;
-    const int64_t gy0 = rc[1] / gh, gy1 = (rc[3] - 1) / gh + 1;
-    total += (gx1 - gx0) * (gy1 - gy0);
-  }
-  return total;
-}
+/* Tile membership. A (splat, tile) pair can matter only where alpha = o e^power >= 1/255, i.e.
+ * inside the ellipse Q(d) = a dx^2 + 2 b dx dy + c dy^2 <= 2 ln(255 o). The rule widens that level
+ * to R = 2 (ln 255 + L(o) + 0.05), with L(o) >= ln(o) read off the float's exponent and mantissa
+ * (L = k ln 2 + ln 2 / 2 if the mantissa is below sqrt 2, else (k + 1) ln 2), and widens every tile's
+ * pixel-centre box [16 tx, 16 tx + 15] x [16 ty, 16 ty + 15] by 1/16 px. The ellipse is convex, so
+ * in the band of tile row ty the tiles it meets are one run [lo, hi]: from the x-extent of the
+ * ellipse inside the band, which is attained at the band's point nearest to the ellipse's
+ * rightmost (leftmost) point, dy = -(b/c) Xmax (+(b/c) Xmax), Xmax = sqrt(R c / det).
+ * Every value is a float and every operation rounds to float on its own (no contraction; the one
+ * fmaf is Kahan's determinant): the CUDA path takes the same decisions bit for bit. */
+#define ORC_MEMBER_EPS 0.0625f
+#define ORC_MEMBER_MARGIN 0.05f
 
 typedef struct {
+  float mx, my, a, b, det, aR, Xmax, Ymax, bc;
+  int all;  /* degenerate conic: keep every tile of the range */
+  int none; /* o < 1/255: no tile */
+} orc_member;
+
+static void member_setup(float mx, float my, float a, float b, float c, float o, orc_member* g) {
+  memset(g, 0, sizeof *g);
+  g->mx = mx;
+  g->my = my;
+  g->a = a;
+  g->b = b;
+  const float w = b * b;
+  const float e = fmaf(-b, b, w); /* w - b b exactly */
+  const float det = fmaf(a, c, -w) + e;
+  if (!(a > 0.0f) || !(c > 0.0f) || !(det > 0.0f)) {
+    g->all = 1;
+    return;
+  }
+  uint32_t bits;
+  memcpy(&bits, &o, sizeof bits);
+  const int32_t ex = (int32_t)((bits >> 23) & 0xFFu);
+  const uint32_t man = bits & 0x7FFFFFu;
+  /* L(o) = halves * (ln 2) / 2; 0x3504F3 is the mantissa of the largest float below sqrt 2 */
+  const int32_t halves = ex == 0 ? -250 : 2 * (ex - 127) + (man <= 0x3504F3u ? 1 : 2);
+  const float L = (float)halves * 0.3465736f;
+  float t = 5.5412636f + L; /* ln 255 */
+  t = t + ORC_MEMBER_MARGIN;
+  const float R = 2.0f * t;
+  if (!(R > 0.0f)) {
+    g->none = 1;
+    return;
+  }
+  const float aR = a * R;
+  const float cR = c * R;
+  g->aR = aR;
+  g->det = det;
+  g->Ymax = sqrtf(aR / det);
+  g->Xmax = sqrtf(cR / det);
+  g->bc = b / c;
+}
+
+static float clampf(float v, float lo, float hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* The tiles [*lo, *hi] of tile row ty the ellipse meets (*lo > *hi: none). */
+static void member_row(const orc_member* g, int32_t ty, int32_t* lo, int32_t* hi) {
+  const float y0 = (float)(16 * ty) - ORC_MEMBER_EPS;
+  const float y1 = (float)(16 * ty + 15) + ORC_MEMBER_EPS;
+  const float dy0 = y0 - g->my;
+  const float dy1 = y1 - g->my;
+  const float nY = -g->Ymax;
+  const float lb = dy0 > nY ? dy0 : nY;
+  const float ub = dy1 < g->Ymax ? dy1 : g->Ymax;
+  if (!(lb <= ub)) {
+    *lo = 1;
+    *hi = 0;
+    return;
+  }
+  const float sx = g->bc * g->Xmax;
+  const float yh = clampf(-sx, lb, ub);
+  const float yl = clampf(sx, lb, ub);
+  const float dh = g->det * yh;
+  const float dl = g->det * yl;
+  const float qh = g->aR - dh * yh;
+  const float ql = g->aR - dl * yl;
+  const float sh = sqrtf(qh > 0.0f ? qh : 0.0f);
+  const float sl = sqrtf(ql > 0.0f ? ql : 0.0f);
+  const float bh = g->b * yh;
+  const float bl = g->b * yl;
+  const float xh = (sh - bh) / g->a;
+  const float xl = (-sl - bl) / g->a;
+  const float xmax = g->mx + xh;
+  const float xmin = g->mx + xl;
+  const float fh = clampf((xmax + ORC_MEMBER_EPS) * 0.0625f, -1e6f, 1e6f);
+  const float fl = clampf((xmin - (15.0f + ORC_MEMBER_EPS)) * 0.0625f, -1e6f, 1e6f);
+  *hi = (int32_t)floorf(fh);
+  *lo = (int32_t)ceilf(fl);
+}
+
+/* Mask of the member tiles of group (gx, gy) that are in the tile range `rc` and, with membership,
+ * meet the splat's ellipse. */
+static uint32_t group_mask(const orc_member* g, const int32_t rc[4], int32_t gx, int32_t gy,
+                           int32_t gw, int32_t gh) {
+  uint32_t mask = 0;
+  for (int32_t ty = gy * gh; ty < (gy + 1) * gh; ++ty) {
+    if (ty < rc[1] || ty >= rc[3]) continue;
+    int32_t lo = rc[0], hi = rc[2] - 1;
+    if (g && !g->all) {
+      if (g->none) continue;
+      int32_t rl, rh;
+      member_row(g, ty, &rl, &rh);
+      if (rl > lo) lo = rl;
+      if (rh < hi) hi = rh;
+    }
+    for (int32_t tx = gx * gw; tx < (gx + 1) * gw; ++tx)
+      if (tx >= lo && tx <= hi) mask |= 1u << ((ty - gy * gh) * gw + (tx - gx * gw));
+  }
+  return mask;
+}
+
+struct orc_entry_s;
+
+/* Counts or fills (when ent != NULL) the entries of every visible splat: one per group of its tile
+ * range whose mask (with membership when conic != NULL) is not empty. */
+static int64_t enumerate_entries(int64_t n, const double* mean2d, const int32_t* radius,
+                                 const double* depth, const double* conic, const double* opacity,
+                                 int32_t width, int32_t height, int32_t gw, int32_t gh, int32_t GX,
+                                 struct orc_entry_s* ent);
+
+int64_t orc_bin_count(int64_t n, const double* mean2d, const int32_t* radius, const double* conic,
+                      const double* opacity, int32_t width, int32_t height, int32_t gw, int32_t gh) {
+  const int32_t GX = ((width + ORC_TILE - 1) / ORC_TILE + gw - 1) / gw;
+  return enumerate_entries(n, mean2d, radius, NULL, conic, opacity, width, height, gw, gh, GX, NULL);
+}
+
+typedef struct orc_entry_s {
   uint64_t key;
   uint32_t val;
   uint16_t mask;
@@ -287,32 +407,44 @@ static uint32_t float_bits(double v) {
   return u;
 }
 
-void orc_bin(int64_t n, const double* mean2d, const int32_t* radius, const double* depth,
-             int32_t width, int32_t height, int32_t gw, int32_t gh, uint64_t* keys, uint32_t* vals,
-             uint16_t* masks, uint32_t* ranges) {
-  int32_t TX, TY, GX, GY;
-  group_grid(width, height, gw, gh, &TX, &TY, &GX, &GY);
-  const int64_t E = orc_bin_count(n, mean2d, radius, width, height, gw, gh);
-  orc_entry* ent = (orc_entry*)malloc((size_t)(E > 0 ? E : 1) * sizeof(orc_entry));
+static int64_t enumerate_entries(int64_t n, const double* mean2d, const int32_t* radius,
+                                 const double* depth, const double* conic, const double* opacity,
+                                 int32_t width, int32_t height, int32_t gw, int32_t gh, int32_t GX,
+                                 orc_entry* ent) {
   int64_t e = 0;
   for (int64_t i = 0; i < n; ++i) {
     if (radius[i] <= 0) continue;
     int32_t rc[4];
     if (!orc_tile_rect(mean2d[2 * i], mean2d[2 * i + 1], radius[i], width, height, rc)) continue;
-    const uint32_t dbits = float_bits(depth[i]);
+    orc_member m;
+    if (conic)
+      member_setup((float)mean2d[2 * i], (float)mean2d[2 * i + 1], (float)conic[3 * i],
+                   (float)conic[3 * i + 1], (float)conic[3 * i + 2], (float)opacity[i], &m);
+    const uint32_t dbits = ent ? float_bits(depth[i]) : 0u;
     for (int32_t gy = rc[1] / gh; gy <= (rc[3] - 1) / gh; ++gy)
       for (int32_t gx = rc[0] / gw; gx <= (rc[2] - 1) / gw; ++gx) {
-        uint32_t mask = 0;
-        for (int32_t ty = gy * gh; ty < (gy + 1) * gh; ++ty)
-          for (int32_t tx = gx * gw; tx < (gx + 1) * gw; ++tx)
-            if (tx >= rc[0] && tx < rc[2] && ty >= rc[1] && ty < rc[3])
-              mask |= 1u << ((ty - gy * gh) * gw + (tx - gx * gw));
-        ent[e].key = ((uint64_t)(uint32_t)(gy * GX + gx) << 32) | dbits;
-        ent[e].val = (uint32_t)i;
-        ent[e].mask = (uint16_t)mask;
+        const uint32_t mask = group_mask(conic ? &m : NULL, rc, gx, gy, gw, gh);
+        if (!mask) continue;
+        if (ent) {
+          ent[e].key = ((uint64_t)(uint32_t)(gy * GX + gx) << 32) | dbits;
+          ent[e].val = (uint32_t)i;
+          ent[e].mask = (uint16_t)mask;
+        }
         ++e;
       }
   }
+  return e;
+}
+
+void orc_bin(int64_t n, const double* mean2d, const int32_t* radius, const double* depth,
+             const double* conic, const double* opacity, int32_t width, int32_t height, int32_t gw,
+             int32_t gh, uint64_t* keys, uint32_t* vals, uint16_t* masks, uint32_t* ranges) {
+  int32_t TX, TY, GX, GY;
+  group_grid(width, height, gw, gh, &TX, &TY, &GX, &GY);
+  const int64_t E = enumerate_entries(n, mean2d, radius, depth, conic, opacity, width, height, gw,
+                                      gh, GX, NULL);
+  orc_entry* ent = (orc_entry*)malloc((size_t)(E > 0 ? E : 1) * sizeof(orc_entry));
+  enumerate_entries(n, mean2d, radius, depth, conic, opacity, width, height, gw, gh, GX, ent);
   qsort(ent, (size_t)E, sizeof(orc_entry), entry_cmp);
   for (int64_t g = 0; g < (int64_t)GX * GY; ++g) ranges[2 * g] = ranges[2 * g + 1] = 0;
   for (int64_t k = 0; k < E; ++k) {

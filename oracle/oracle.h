@@ -49,16 +49,18 @@ void orc_project_cov(const float* mean, const float* scale, const float* quat,
 int32_t orc_tile_rect(double mx, double my, int32_t r, int32_t width, int32_t height,
                       int32_t rect[4]);
 
-/* Number of group-level entries (Section 4.4.2: one entry per overlapped tile group). */
-int64_t orc_bin_count(int64_t n, const double* mean2d, const int32_t* radius, int32_t width,
-                      int32_t height, int32_t gw, int32_t gh);
+/* Number of group-level entries (Section 4.4.2: one entry per overlapped tile group whose mask is
+ * not empty). conic [n,3] and opacity [n] (FP32 values) switch on the tile-membership test (see
+ * oracle.c); NULL keeps every tile of the AABB's range. */
+int64_t orc_bin_count(int64_t n, const double* mean2d, const int32_t* radius, const double* conic,
+                      const double* opacity, int32_t width, int32_t height, int32_t gw, int32_t gh);
 
 /* Group-level entries with tile-membership masks, sorted by (group ID, depth) (Section 4.4.2,
  * Algorithm 1). keys = (gid << 32) | bits(float(depth)); ties by splat index. ranges[2g], ranges[2g+1]
- * = [start, end) of group g. */
+ * = [start, end) of group g. conic / opacity as in orc_bin_count. */
 void orc_bin(int64_t n, const double* mean2d, const int32_t* radius, const double* depth,
-             int32_t width, int32_t height, int32_t gw, int32_t gh, uint64_t* keys, uint32_t* vals,
-             uint16_t* masks, uint32_t* ranges);
+             const double* conic, const double* opacity, int32_t width, int32_t height, int32_t gw,
+             int32_t gh, uint64_t* keys, uint32_t* vals, uint16_t* masks, uint32_t* ranges);
 
 /* Front-to-back blending of every pixel (Section 2 Eqs. power_d, power, alpha, blend; pruning and
  * early termination). If pix != NULL only the npix listed pixels (x, y pairs) are computed and the

@@ -543,3 +543,110 @@ def test_backward_early_termination(orc):
         assert g.opacity[k] == 0.0 and np.all(g.conic[k] == 0.0) and np.all(g.mean2d[k] == 0.0)
         assert np.all(g.rgb[k] == 0.0)
     assert np.all(g.opacity[:3] != 0.0)
+
+
+# ------------------------------------------------------------------------------------------------
+# Tile membership at binning time (beyond the paper): a tile stays in a splat's entry only if the
+# splat can reach alpha >= 1/255 there.
+
+def _membership_case(seed, n=400, W=150, H=110):
+    """Projected splats of every shape: round and needle-like conics at every orientation, tiny
+    and large, opacities from just above 1/255 to 0.99, centres on and off screen."""
+    rng = np.random.default_rng(seed)
+    mean2d = np.stack([rng.uniform(-20, W + 20, n), rng.uniform(-20, H + 20, n)], 1).astype(np.float32)
+    s_major = np.exp(rng.uniform(np.log(0.6), np.log(40.0), n))
+    ratio = np.where(rng.random(n) < 0.3, rng.uniform(20, 400, n), rng.uniform(1, 3, n))
+    s_minor = np.maximum(s_major / ratio, 0.55)
+    th = rng.uniform(0, np.pi, n)
+    cth, sth = np.cos(th), np.sin(th)
+    # covariance = Rot diag(s_major^2, s_minor^2) Rot^T; conic = its inverse
+    cxx = cth ** 2 * s_major ** 2 + sth ** 2 * s_minor ** 2
+    cyy = sth ** 2 * s_major ** 2 + cth ** 2 * s_minor ** 2
+    cxy = cth * sth * (s_major ** 2 - s_minor ** 2)
+    det = cxx * cyy - cxy ** 2
+    conic = np.stack([cyy / det, -cxy / det, cxx / det], 1).astype(np.float32)
+    opac = np.where(rng.random(n) < 0.15, rng.uniform(1.0 / 255, 0.02, n), rng.uniform(0.02, 0.99, n))
+    opac = opac.astype(np.float32)
+    radius = np.ceil(3 * np.sqrt(0.5 * (cxx + cyy) + np.sqrt(np.maximum(0.1, (0.5 * (cxx - cyy)) ** 2
+                                                                         + cxy ** 2)))).astype(np.int32)
+    depth = rng.uniform(1, 5, n).astype(np.float32)
+    return mean2d, conic, opac, radius, depth, W, H
+
+
+def _pairs(orc, b, W, H):
+    """(splat, tx, ty) of every set mask bit."""
+    TX, TY, GX, GY = orc.group_grid(W, H, b.gw, b.gh)
+    out = set()
+    for k in range(b.num_entries):
+        g = int(b.keys[k] >> 32)
+        gx, gy = g % GX, g // GX
+        for bit in range(b.gw * b.gh):
+            if int(b.masks[k]) >> bit & 1:
+                out.add((int(b.vals[k]), gx * b.gw + bit % b.gw, gy * b.gh + bit // b.gw))
+    return out
+
+
+def _max_alpha_in_tile(mean2d, conic, opac, i, tx, ty, W, H):
+    xs = np.arange(tx * 16, min(tx * 16 + 16, W), dtype=np.float64)
+    ys = np.arange(ty * 16, min(ty * 16 + 16, H), dtype=np.float64)
+    X, Y = np.meshgrid(xs, ys)
+    a, b, c = conic[i].astype(np.float64)
+    dx, dy = X - float(mean2d[i, 0]), Y - float(mean2d[i, 1])
+    power = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy
+    return float(opac[i]) * float(np.exp(power.max()))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_membership_drops_only_pairs_below_the_pruning_threshold(orc, seed):
+    mean2d, conic, opac, radius, depth, W, H = _membership_case(seed)
+    rect_only = orc.bin_sort(mean2d, radius, depth, W, H, 1, 1)
+    member = orc.bin_sort(mean2d, radius, depth, W, H, 1, 1, conic=conic, opacity=opac)
+    all_pairs, kept = _pairs(orc, rect_only, W, H), _pairs(orc, member, W, H)
+    assert kept <= all_pairs
+    dropped = all_pairs - kept
+    assert len(dropped) > 0.3 * len(all_pairs)  # the rule does cull
+    # conservative: every dropped pair is pruned at every pixel centre of its tile (FP64 brute force)
+    for (i, tx, ty) in dropped:
+        assert _max_alpha_in_tile(mean2d, conic, opac, i, tx, ty, W, H) < 1.0 / 255.0, (i, tx, ty)
+    # tight: the pairs kept although no pixel of the tile reaches 1/255 are a small minority
+    dead_kept = sum(1 for (i, tx, ty) in kept
+                    if _max_alpha_in_tile(mean2d, conic, opac, i, tx, ty, W, H) < 1.0 / 255.0)
+    dead = dead_kept + len(dropped)
+    assert dead_kept < 0.15 * dead, (dead_kept, dead)
+
+
+@pytest.mark.parametrize("gw,gh", [(2, 2), (4, 2), (4, 4), (3, 1)])
+def test_membership_does_not_depend_on_grouping(orc, gw, gh):
+    # the kept (splat, tile) pairs are a property of the splat and the tile alone
+    mean2d, conic, opac, radius, depth, W, H = _membership_case(9)
+    one = orc.bin_sort(mean2d, radius, depth, W, H, 1, 1, conic=conic, opacity=opac)
+    grp = orc.bin_sort(mean2d, radius, depth, W, H, gw, gh, conic=conic, opacity=opac)
+    assert _pairs(orc, grp, W, H) == _pairs(orc, one, W, H)
+    assert np.all(grp.masks != 0)
+
+
+def test_membership_leaves_the_image_unchanged(orc):
+    # dropped pairs would be pruned at every pixel: colour and transmittance are bit-identical, the
+    # passing pairs are the same, only pairs that fail the 1/255 test disappear from the lists
+    scene = scenes.mixture_scene(6000, seed=4, components=8, cluster_std=0.3, radius=1.5,
+                                 log_scale_mean=-3.2, sh_degree=1, needle_fraction=0.2)
+    cam = scenes.orbit_cameras(4, 4.0, 200, 150)[1]
+    pr = orc.preprocess(scene, cam)
+    for gw, gh in ((1, 1), (2, 2)):
+        plain = orc.bin_sort(pr.mean2d, pr.radius, pr.depth, 200, 150, gw, gh)
+        memb = orc.bin_sort(pr.mean2d, pr.radius, pr.depth, 200, 150, gw, gh, conic=pr.conic,
+                            opacity=pr.opacity)
+        assert memb.num_entries < plain.num_entries
+        i0 = orc.blend(200, 150, pr.mean2d, pr.conic, pr.opacity, pr.rgb, plain, bg=(0.1, 0.2, 0.3))
+        i1 = orc.blend(200, 150, pr.mean2d, pr.conic, pr.opacity, pr.rgb, memb, bg=(0.1, 0.2, 0.3))
+        assert np.array_equal(i0.rgb, i1.rgb) and np.array_equal(i0.T, i1.T)
+        assert i0.passing == i1.passing and i1.evaluated < i0.evaluated
+        # n_contrib counts list positions: the last blended splat is the same one
+        _, _, GX, _ = orc.group_grid(200, 150, gw, gh)
+        for y in range(0, 150, 7):
+            for x in range(0, 200, 7):
+                g = ((y // 16) // gh) * GX + (x // 16) // gw
+                n0, n1 = int(i0.n_contrib[y, x]), int(i1.n_contrib[y, x])
+                assert (n0 == 0) == (n1 == 0)
+                if n0:
+                    assert plain.vals[plain.ranges[g][0] + n0 - 1] == memb.vals[memb.ranges[g][0] + n1 - 1]
