@@ -146,7 +146,8 @@ def cpu_baseline(scene, cam, tc_image=None, target_s=12.0, seed=0):
     t0 = time.perf_counter()
     pr = oracle.preprocess(scene, cam)
     t1 = time.perf_counter()
-    bins = oracle.bin_sort(pr.mean2d, pr.radius, pr.depth, cam.width, cam.height, 2, 2)
+    bins = oracle.bin_sort(pr.mean2d, pr.radius, pr.depth, cam.width, cam.height, 2, 2, conic=pr.conic,
+                           opacity=pr.opacity)
     t2 = time.perf_counter()
     TX, TY, GX, GY = oracle.group_grid(cam.width, cam.height, 2, 2)
     rng = np.random.default_rng(seed)
@@ -323,7 +324,8 @@ def _oracle_sample(scene, cam, target_s=10.0, seed=0):
     oracle blending): (pixels [P,2] as (x, y), rgb [P,3])."""
     import oracle
     pr = oracle.preprocess(scene, cam)
-    bins = oracle.bin_sort(pr.mean2d, pr.radius, pr.depth, cam.width, cam.height, 2, 2)
+    bins = oracle.bin_sort(pr.mean2d, pr.radius, pr.depth, cam.width, cam.height, 2, 2, conic=pr.conic,
+                           opacity=pr.opacity)
     TX, TY, GX, GY = oracle.group_grid(cam.width, cam.height, 2, 2)
     rng = np.random.default_rng(seed)
     order = rng.permutation(GX * GY)

@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define TGS_ABI_VERSION 1
+#define TGS_ABI_VERSION 2
 #define TGS_TILE 16
 #define TGS_MAX_GROUP 4
 
@@ -80,8 +80,13 @@ typedef struct {
   float near_z;           /* Gaussians with camera-space z <= near_z are culled */
 } tgs_camera;
 
+/* Flags of tgs_tiling. */
+#define TGS_BIN_RANGE_ONLY 1 /* keep every tile of a Gaussian's AABB tile range (no membership
+                                test; for measuring the test, the image is the same) */
+
 typedef struct {
   int32_t group_w, group_h; /* tiles per group along x and y, each 1..TGS_MAX_GROUP */
+  int32_t flags;            /* TGS_BIN_*; 0 = tile membership on */
 } tgs_tiling;
 
 /* Projected Gaussians: caller-allocated device arrays of length n (written by tgs_preprocess,
@@ -148,14 +153,21 @@ tgs_status tgs_preprocess(const tgs_scene* scene, const tgs_camera* cam, tgs_pro
 tgs_status tgs_bin_sort_workspace_size(int64_t n, int64_t capacity, int32_t width, int32_t height,
                                        const tgs_tiling* tiling, size_t* bytes);
 
-/* Bin and sort (Section 4.4.2; Algorithm 1): one entry per (Gaussian, overlapped tile group) with
- * the mask of the group's member tiles inside the Gaussian's tile range, sorted ascending by
- * (group id, float depth, Gaussian index) -- the 64-bit key (gid << 32) | depth bits with ties by
- * index. Fills keys (if non-NULL), vals, masks, ranges and *num_entries. If the frame needs more
- * than `capacity` entries, nothing is emitted, every range is (0, 0) and *num_entries holds the
- * needed count. If num_entries_host != NULL the call copies the count to it, synchronizes `stream`
- * and returns TGS_ERR_CAPACITY on overflow; otherwise it is fully asynchronous.
- * `workspace` is device memory of at least tgs_bin_sort_workspace_size bytes, 256-byte aligned. */
+/* Bin and sort (Section 4.4.2; Algorithm 1): one entry per (Gaussian, tile group) whose mask of
+ * member tiles is not empty, sorted ascending by (group id, float depth, Gaussian index) -- the
+ * 64-bit key (gid << 32) | depth bits with ties by index. A tile of the Gaussian's AABB tile range
+ * is a member unless the Gaussian provably cannot reach alpha >= 1/255 at any of its pixels (beyond
+ * the paper, whose Section 6 cites tighter footprints; the rasterized image is the same; turned off
+ * by TGS_BIN_RANGE_ONLY): the Gaussian's ellipse at the level o e^power = e^-0.05 / 255, with o
+ * bounded from above by a half power of two, must meet the tile's pixel-centre box widened by 1/16
+ * px, tested in FP32 with a fixed operation order. The mask bit of tile (tx, ty) is
+ * (ty % gh) * gw + (tx % gw). Fills keys (if non-NULL), vals, masks, ranges and *num_entries (the
+ * frame's entry count). Reads proj->rect, depth, radius and, for the membership test, mean2d and
+ * conic_opacity. If the frame needs more than `capacity` entries, nothing is emitted, every range
+ * is (0, 0) and *num_entries holds the needed count. If num_entries_host != NULL the call copies
+ * the count to it, synchronizes `stream` and returns TGS_ERR_CAPACITY on overflow; otherwise it is
+ * fully asynchronous. `workspace` is device memory of at least tgs_bin_sort_workspace_size bytes,
+ * 256-byte aligned. */
 tgs_status tgs_bin_sort(const tgs_projected* proj, int64_t n, int32_t width, int32_t height,
                         const tgs_tiling* tiling, void* workspace, size_t workspace_bytes,
                         tgs_bins* bins, int64_t* num_entries_host, void* stream);

@@ -272,7 +272,7 @@ static void group_grid(int32_t width, int32_t height, int32_t gw, int32_t gh, in
 #define ORC_MEMBER_MARGIN 0.05f
 
 typedef struct {
-  float mx, my, a, b, det, aR, Xmax, Ymax, bc;
+  float mx, my, ia, b, det, aR, Xmax, Ymax, bc;
   int all;  /* degenerate conic: keep every tile of the range */
   int none; /* o < 1/255: no tile */
 } orc_member;
@@ -281,7 +281,6 @@ static void member_setup(float mx, float my, float a, float b, float c, float o,
   memset(g, 0, sizeof *g);
   g->mx = mx;
   g->my = my;
-  g->a = a;
   g->b = b;
   const float w = b * b;
   const float e = fmaf(-b, b, w); /* w - b b exactly */
@@ -311,6 +310,7 @@ static void member_setup(float mx, float my, float a, float b, float c, float o,
   g->Ymax = sqrtf(aR / det);
   g->Xmax = sqrtf(cR / det);
   g->bc = b / c;
+  g->ia = 1.0f / a;
 }
 
 static float clampf(float v, float lo, float hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -340,8 +340,8 @@ static void member_row(const orc_member* g, int32_t ty, int32_t* lo, int32_t* hi
   const float sl = sqrtf(ql > 0.0f ? ql : 0.0f);
   const float bh = g->b * yh;
   const float bl = g->b * yl;
-  const float xh = (sh - bh) / g->a;
-  const float xl = (-sl - bl) / g->a;
+  const float xh = (sh - bh) * g->ia;
+  const float xl = (-sl - bl) * g->ia;
   const float xmax = g->mx + xh;
   const float xmin = g->mx + xl;
   const float fh = clampf((xmax + ORC_MEMBER_EPS) * 0.0625f, -1e6f, 1e6f);

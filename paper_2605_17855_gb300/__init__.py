@@ -57,7 +57,10 @@ class _Camera(C.Structure):
 
 
 class _Tiling(C.Structure):
-    _fields_ = [("group_w", C.c_int32), ("group_h", C.c_int32)]
+    _fields_ = [("group_w", C.c_int32), ("group_h", C.c_int32), ("flags", C.c_int32)]
+
+
+BIN_RANGE_ONLY = 1  # tgs_tiling.flags: no tile-membership test
 
 
 class _Projected(C.Structure):
@@ -219,9 +222,9 @@ def camera_struct(cam) -> _Camera:
     return c
 
 
-def _tiling(tiling) -> _Tiling:
-    gw, gh = tiling
-    return _Tiling(int(gw), int(gh))
+def _tiling(tiling, membership: bool = True) -> _Tiling:
+    gw, gh = tiling[:2]
+    return _Tiling(int(gw), int(gh), 0 if membership else BIN_RANGE_ONLY)
 
 
 def group_grid(width, height, tiling):
@@ -278,6 +281,7 @@ class Bins:
     num_entries: "object"  # [1] int64 (device)
     workspace: "object"    # uint8 workspace
     entries: int = -1      # host copy of the count when known
+    membership: bool = True  # the tile-membership test was on (tgs_tiling.flags)
 
     def struct(self) -> _Bins:
         return _Bins(self.capacity, _ptr(self.keys), _ptr(self.vals), _ptr(self.masks), _ptr(self.ranges),
@@ -307,16 +311,18 @@ def allocate_bins(n, capacity, width, height, tiling, device="cuda", keys=True) 
 
 
 def bin_sort(proj: Projected, width, height, tiling=(2, 2), bins: Bins | None = None, capacity=None,
-             sync=True, stream=None) -> Bins:
+             sync=True, stream=None, membership=True) -> Bins:
     """Bins and sorts. With sync=True the entry count is read back (one stream sync) and the
     capacity grows as needed; with sync=False the call is fully asynchronous and overflow leaves
-    every range empty (check bins.num_entries)."""
+    every range empty (check bins.num_entries). membership=False keeps every tile of each
+    Gaussian's AABB range (TGS_BIN_RANGE_ONLY)."""
     lib = load()
     n = proj.n
     if bins is None:
         bins = allocate_bins(n, capacity if capacity is not None else max(1024, 8 * n), width, height,
                              tiling, proj.mean2d.device)
-    t = _tiling(tiling)
+    t = _tiling(tiling, membership)
+    bins.membership = bool(membership)
     while True:
         b = bins.struct()
         host = C.c_int64(0)
@@ -326,6 +332,7 @@ def bin_sort(proj: Projected, width, height, tiling=(2, 2), bins: Bins | None = 
         if sync and st == TGS_ERR_CAPACITY:
             bins = allocate_bins(n, int(host.value * 1.25) + 1024, width, height, tiling,
                                  proj.mean2d.device, keys=bins.keys is not None)
+            bins.membership = bool(membership)
             continue
         _check(st)
         if sync:
@@ -338,7 +345,7 @@ def bin_sort_static(proj: Projected, width, height, bins: Bins, sync=True, strea
     bins.workspace (for callers that must not allocate device memory). `bins` must already be
     allocated with enough capacity."""
     lib = load()
-    t = _tiling(bins.tiling)
+    t = _tiling(bins.tiling, bins.membership)
     host = C.c_int64(0)
     _check(lib.tgs_bin_sort_static(C.byref(proj.struct()), proj.n, int(width), int(height), C.byref(t),
                                    C.byref(bins.struct()), C.byref(host) if sync else None, _stream(stream)))
@@ -453,8 +460,9 @@ class Renderer:
     """
 
     def __init__(self, scene: DeviceScene, cameras, tiling=(2, 2), precision="fp16_tc",
-                 bg=(0.0, 0.0, 0.0), margin=1.1, graphs=True, cull=True, pipeline=True):
+                 bg=(0.0, 0.0, 0.0), margin=1.1, graphs=True, cull=True, pipeline=True, membership=True):
         self.cull = cull
+        self.membership = membership
         self.scene, self.cameras = scene, list(cameras)
         self.tiling, self.precision, self.bg = tuple(tiling), precision, tuple(bg)
         self.pipeline = bool(pipeline)
@@ -466,7 +474,8 @@ class Renderer:
         cap = 0
         for cam in self.cameras:
             preprocess(scene, cam, out=self.proj)
-            cap = max(cap, bin_sort(self.proj, cam.width, cam.height, self.tiling).entries)
+            cap = max(cap, bin_sort(self.proj, cam.width, cam.height, self.tiling,
+                                    membership=membership).entries)
         W = max(c.width for c in self.cameras)
         H = max(c.height for c in self.cameras)
         # bin buffers are shared by the cameras of a set (ranges sized for the largest image)
@@ -509,7 +518,8 @@ class Renderer:
         cam = self.cameras[k]
         proj, bins = self.proj_sets[self._set(k)], self.bin_sets[self._set(k)]
         preprocess(self.scene, cam, out=proj)
-        bin_sort(proj, cam.width, cam.height, self.tiling, bins=bins, sync=False)
+        bin_sort(proj, cam.width, cam.height, self.tiling, bins=bins, sync=False,
+                 membership=self.membership)
 
     def _raster(self, k):
         cam = self.cameras[k]

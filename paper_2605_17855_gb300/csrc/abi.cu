@@ -61,7 +61,7 @@ int32_t* device_error_word() {
 
 static bool valid_tiling(const tgs_tiling* t) {
   return t && t->group_w >= 1 && t->group_w <= TGS_MAX_GROUP && t->group_h >= 1 &&
-         t->group_h <= TGS_MAX_GROUP;
+         t->group_h <= TGS_MAX_GROUP && (t->flags & ~TGS_BIN_RANGE_ONLY) == 0;
 }
 
 static bool valid_size(int32_t w, int32_t h) { return w >= 1 && h >= 1 && w <= 16384 && h <= 16384; }
@@ -170,8 +170,9 @@ tgs_status tgs_bin_sort(const tgs_projected* proj, int64_t n, int32_t width, int
   tgs_status s = require_current_sm103();
   if (s != TGS_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
-  s = launch_bin_sort(*proj, n, width, height, tiling->group_w, tiling->group_h, workspace,
-                      workspace_bytes, *bins, st);
+  s = launch_bin_sort(*proj, n, width, height, tiling->group_w, tiling->group_h,
+                      (tiling->flags & TGS_BIN_RANGE_ONLY) == 0, workspace, workspace_bytes, *bins,
+                      st);
   if (s != TGS_OK || !num_entries_host) return s;
   TGS_CUDA(cudaMemcpyAsync(num_entries_host, bins->num_entries, sizeof(int64_t),
                            cudaMemcpyDeviceToHost, st));

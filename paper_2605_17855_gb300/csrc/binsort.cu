@@ -8,12 +8,22 @@
 // duplication; the duplicates are then emitted in that depth order and stably sorted by group id
 // alone (ceil(log2 G / 8) passes over E items). A stable LSD sort is exactly this composition.
 //
-// Stages (all kernels HBM-bound; sizes taken from device memory so no host round trip is needed):
-//   depth keys + their digit histograms -> 4 radix passes -> exclusive prefix of the per-Gaussian
-//   group counts (total = needed entries), with the per-group entry counts accumulated as a 2D
-//   difference array -> group table (group ranges, histograms of the group-id digits) -> emit
-//   (gid, index) in depth order -> radix passes over the group-id digits -> masks (from the tile
-//   ranges) and the optional 64-bit keys.
+// Tile membership (beyond the paper; Section 6 cites tighter splat footprints as related work):
+// a tile of a Gaussian's AABB tile range is a member only if the Gaussian's ellipse at the level
+// where o e^power could reach 1/255 (widened for safety) meets the tile's pixel-centre box; an
+// entry is emitted for a group only if one of its tiles is a member, and its mask holds the
+// member tiles. A dropped (Gaussian, tile) pair fails the pruning test at every pixel of the
+// tile, so the image does not change; the lists, the sort and the rasterizer's gathers shrink.
+// Per tile row the member tiles are one run (the ellipse is convex), found from the ellipse's
+// x-extent in the row's band; the test is a decision about which entries exist, taken in FP32
+// with every operation rounded on its own in a fixed order, so that it is reproducible bit for bit.
+//
+// Stages (sizes read from device memory, so no host round trip is needed):
+//   depth keys of the visible Gaussians + their digit histograms -> 4 radix passes (depth order)
+//   -> per Gaussian, its number of entries (O(tile rows) of arithmetic) -> exclusive prefix of the
+//   counts (total = entries the frame needs) -> emit (group id, index, mask) in depth order, with
+//   the histograms of the group-id digits -> radix passes over the group-id digits carrying index
+//   and mask -> group ranges from the sorted group ids (and the optional 64-bit keys).
 // Every radix pass and the prefix are single kernels: a tile's offsets come from the earlier tiles
 // by decoupled look-back (bounded waits) instead of separate histogram and scan kernels.
 #include <algorithm>
@@ -168,28 +178,219 @@ __device__ uint64_t lookback64_warp(uint64_t* status, int tile, uint64_t mine, i
   return excl;
 }
 
-// The per-entry outputs besides the Gaussian index: the mask of the group's member tiles inside the
-// Gaussian's tile range and, optionally, the 64-bit key.
-struct Finalize {
-  const int4* rect;
-  const float* depth;
-  int gw, gh, GX;
-  uint16_t* masks;
-  uint64_t* keys64;  // may be NULL
+// ---------------------------------------------------------------------------------------------
+// Tile membership. With Q(d) = a dx^2 + 2 b dx dy + c dy^2 (the conic), a pair can matter only where
+// o e^(-Q/2) >= 1/255. The test uses the level R = 2 (ln 255 + L(o) + kMemberMargin) with L(o) >=
+// ln(o) read off the float's exponent and mantissa (k ln 2 + ln 2 / 2 if the mantissa is below
+// sqrt 2, else (k + 1) ln 2) and widens every tile's pixel-centre box by kMemberEps px. In the band
+// of tile row ty the ellipse Q <= R spans x in [xmin, xmax], attained at the band's points nearest
+// to the ellipse's leftmost and rightmost points (dy = +-(b/c) Xmax, Xmax = sqrt(R c / det)); the
+// member tiles of the row are the run whose widened boxes meet that span. Every operation is a
+// single IEEE-rounded FP32 operation in a fixed order (the _rn intrinsics; one FMA pair for Kahan's
+// determinant), so the result is reproducible bit for bit.
+constexpr float kMemberEps = 0.0625f;
+constexpr float kMemberMargin = 0.05f;
+
+struct Member {
+  float mx, my, ia, b, det, aR, Xmax, Ymax, bc;
+  bool all;   // degenerate conic: every tile of the range is a member
+  bool none;  // o < 1/255: no tile is
 };
 
-__device__ __forceinline__ void entry_outputs(const Finalize& f, uint32_t pos, uint32_t g,
-                                              uint32_t i) {
-  const int4 r = f.rect[i];
-  const int gx = (int)(g % (uint32_t)f.GX), gy = (int)(g / (uint32_t)f.GX);
-  uint32_t m = 0;
-  for (int ty = 0; ty < f.gh; ++ty)
-    for (int tx = 0; tx < f.gw; ++tx) {
-      const int X = gx * f.gw + tx, Y = gy * f.gh + ty;
-      if (X >= r.x && X < r.z && Y >= r.y && Y < r.w) m |= 1u << (ty * f.gw + tx);
+__device__ __forceinline__ float clamp_rn(float v, float lo, float hi) {
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+
+__device__ __forceinline__ Member member_setup(float2 mu, float4 co) {
+  Member g;
+  g.mx = mu.x;
+  g.my = mu.y;
+  g.b = co.y;
+  g.all = false;
+  g.none = false;
+  g.ia = g.det = g.aR = g.Xmax = g.Ymax = g.bc = 0.f;
+  const float w = __fmul_rn(co.y, co.y);
+  const float e = __fmaf_rn(-co.y, co.y, w);
+  const float det = __fadd_rn(__fmaf_rn(co.x, co.z, -w), e);
+  if (!(co.x > 0.f) || !(co.z > 0.f) || !(det > 0.f)) {
+    g.all = true;
+    return g;
+  }
+  const uint32_t bits = __float_as_uint(co.w);
+  const int ex = (int)((bits >> 23) & 0xFFu);
+  const uint32_t man = bits & 0x7FFFFFu;
+  // L(o) = halves * (ln 2) / 2; 0x3504F3 is the mantissa of the largest float below sqrt 2
+  const int halves = ex == 0 ? -250 : 2 * (ex - 127) + (man <= 0x3504F3u ? 1 : 2);
+  const float L = __fmul_rn((float)halves, 0.3465736f);
+  float t = __fadd_rn(5.5412636f, L);  // ln 255
+  t = __fadd_rn(t, kMemberMargin);
+  const float R = __fmul_rn(2.0f, t);
+  if (!(R > 0.f)) {
+    g.none = true;
+    return g;
+  }
+  const float aR = __fmul_rn(co.x, R);
+  const float cR = __fmul_rn(co.z, R);
+  g.aR = aR;
+  g.det = det;
+  g.Ymax = __fsqrt_rn(__fdiv_rn(aR, det));
+  g.Xmax = __fsqrt_rn(__fdiv_rn(cR, det));
+  g.bc = __fdiv_rn(co.y, co.z);
+  g.ia = __fdiv_rn(1.0f, co.x);
+  return g;
+}
+
+// Member tiles [lo, hi] of tile row ty (lo > hi: none), before clipping to the tile range.
+__device__ __forceinline__ int2 member_row(const Member& g, int ty) {
+  const float y0 = __fsub_rn((float)(16 * ty), kMemberEps);
+  const float y1 = __fadd_rn((float)(16 * ty + 15), kMemberEps);
+  const float dy0 = __fsub_rn(y0, g.my);
+  const float dy1 = __fsub_rn(y1, g.my);
+  const float nY = -g.Ymax;
+  const float lb = dy0 > nY ? dy0 : nY;
+  const float ub = dy1 < g.Ymax ? dy1 : g.Ymax;
+  if (!(lb <= ub)) return make_int2(1, 0);
+  const float sx = __fmul_rn(g.bc, g.Xmax);
+  const float yh = clamp_rn(-sx, lb, ub);
+  const float yl = clamp_rn(sx, lb, ub);
+  const float qh = __fsub_rn(g.aR, __fmul_rn(__fmul_rn(g.det, yh), yh));
+  const float ql = __fsub_rn(g.aR, __fmul_rn(__fmul_rn(g.det, yl), yl));
+  const float sh = __fsqrt_rn(qh > 0.f ? qh : 0.f);
+  const float sl = __fsqrt_rn(ql > 0.f ? ql : 0.f);
+  const float xh = __fmul_rn(__fsub_rn(sh, __fmul_rn(g.b, yh)), g.ia);
+  const float xl = __fmul_rn(__fsub_rn(-sl, __fmul_rn(g.b, yl)), g.ia);
+  const float xmax = __fadd_rn(g.mx, xh);
+  const float xmin = __fadd_rn(g.mx, xl);
+  const float fh = clamp_rn(__fmul_rn(__fadd_rn(xmax, kMemberEps), 0.0625f), -1e6f, 1e6f);
+  const float fl = clamp_rn(__fmul_rn(__fsub_rn(xmin, 15.0f + kMemberEps), 0.0625f), -1e6f, 1e6f);
+  return make_int2((int)ceilf(fl), (int)floorf(fh));
+}
+
+// Member tiles of row ty clipped to the tile range r (lo > hi: none); `use` = membership on.
+__device__ __forceinline__ int2 row_run(const Member& g, bool use, const int4& r, int ty) {
+  int lo = r.x, hi = r.z - 1;
+  if (use && !g.all) {
+    if (g.none) return make_int2(1, 0);
+    const int2 m = member_row(g, ty);
+    lo = max(lo, m.x);
+    hi = min(hi, m.y);
+  }
+  return make_int2(lo, hi);
+}
+
+// The member runs of the (up to TGS_MAX_GROUP) tile rows of group row gy, clipped to the tile
+// range (lo > hi: none).
+struct RowRuns {
+  int lo[TGS_MAX_GROUP], hi[TGS_MAX_GROUP];
+};
+
+__device__ __forceinline__ RowRuns row_runs(const Member& g, bool use, const int4& r, int gy, int gh) {
+  RowRuns q;
+#pragma unroll
+  for (int t = 0; t < TGS_MAX_GROUP; ++t) {
+    const int ty = gy * gh + t;
+    int2 run = make_int2(1, 0);
+    if (t < gh && ty >= r.y && ty < r.w) run = row_run(g, use, r, ty);
+    q.lo[t] = run.x;
+    q.hi[t] = run.y;
+  }
+  return q;
+}
+
+__device__ __forceinline__ void cswap(int& s0, int& e0, int& s1, int& e1) {
+  if (s1 < s0) {
+    const int ts = s0, te = e0;
+    s0 = s1; e0 = e1; s1 = ts; e1 = te;
+  }
+}
+
+// Number of groups of the row holding a member tile: the length of the union of the tile rows'
+// group-column runs [lo / gw, hi / gw] (sorted by a 4-input network, then swept).
+__device__ __forceinline__ uint32_t row_group_count(const RowRuns& q, int gw) {
+  int s[TGS_MAX_GROUP], e[TGS_MAX_GROUP];
+#pragma unroll
+  for (int t = 0; t < TGS_MAX_GROUP; ++t) {
+    const bool ok = q.lo[t] <= q.hi[t];
+    s[t] = ok ? q.lo[t] / gw : 0x7fffffff;
+    e[t] = ok ? q.hi[t] / gw : -1;
+  }
+  static_assert(TGS_MAX_GROUP == 4, "sorting network for four runs");
+  cswap(s[0], e[0], s[1], e[1]);
+  cswap(s[2], e[2], s[3], e[3]);
+  cswap(s[0], e[0], s[2], e[2]);
+  cswap(s[1], e[1], s[3], e[3]);
+  cswap(s[1], e[1], s[2], e[2]);
+  uint32_t total = 0;
+  int end = -1;
+#pragma unroll
+  for (int t = 0; t < TGS_MAX_GROUP; ++t) {
+    if (e[t] < s[t]) continue;  // empty (sorted last)
+    if (s[t] > end) {
+      total += (uint32_t)(e[t] - s[t] + 1);
+      end = e[t];
+    } else if (e[t] > end) {
+      total += (uint32_t)(e[t] - end);
+      end = e[t];
     }
-  f.masks[pos] = (uint16_t)m;
-  if (f.keys64) f.keys64[pos] = ((uint64_t)g << 32) | __float_as_uint(f.depth[i]);
+  }
+  return total;
+}
+
+// Member-tile mask of group gx of the row, bit (ty - gy gh) gw + (tx - gx gw).
+__device__ __forceinline__ uint32_t row_group_mask(const RowRuns& q, int gx, int gw) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int t = 0; t < TGS_MAX_GROUP; ++t) {
+    const int lo = max(q.lo[t], gx * gw), hi = min(q.hi[t], gx * gw + gw - 1);
+    for (int tx = lo; tx <= hi; ++tx) m |= 1u << (t * gw + (tx - gx * gw));
+  }
+  return m;
+}
+
+// The warp's view of one visible Gaussian (lane j holds Gaussian j of the warp's 32): its index,
+// tile range, membership constants and number of group rows (0 if it has no entry).
+struct WarpGauss {
+  uint32_t i;
+  int4 r;
+  Member g;
+  uint32_t rows;
+};
+
+__device__ __forceinline__ WarpGauss warp_gauss(int64_t s, int64_t n, const uint32_t* order,
+                                                const int4* rect, const float2* mean2d,
+                                                const float4* conic_opacity, int gh, bool use) {
+  WarpGauss w{};
+  w.i = 0;
+  w.r = make_int4(0, 0, 0, 0);
+  w.rows = 0;
+  if (s < n) {
+    w.i = order[s];
+    w.r = rect[w.i];
+    if (w.r.z > w.r.x && w.r.w > w.r.y) {
+      if (use) w.g = member_setup(mean2d[w.i], conic_opacity[w.i]);
+      if (!(use && w.g.none)) w.rows = (uint32_t)((w.r.w - 1) / gh - w.r.y / gh + 1);
+    }
+  }
+  return w;
+}
+
+// Smallest lane whose inclusive prefix exceeds k.
+__device__ __forceinline__ int find_src(uint32_t incl, uint32_t k) {
+  int lo = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    const uint32_t v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+    if (v <= k) lo += step;
+  }
+  return lo;
+}
+
+// Sum, over the lanes [lo_k - k0, hi_k - k0) of a round, of the values whose warp inclusive scan is
+// S (hi_k > lo_k, both inside the round).
+__device__ __forceinline__ uint32_t lanes_sum(uint32_t S, uint32_t lo_k, uint32_t hi_k, uint32_t k0) {
+  const uint32_t hi_v = __shfl_sync(0xffffffffu, S, (int)(hi_k - 1 - k0));
+  const uint32_t lo_v = __shfl_sync(0xffffffffu, S, (int)(lo_k > k0 ? lo_k - 1 - k0 : 0));
+  return hi_v - (lo_k > k0 ? lo_v : 0u);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -201,10 +402,12 @@ __device__ __forceinline__ void entry_outputs(const Finalize& f, uint32_t pos, u
 // global start of the digit plus the counts of that digit in the earlier tiles (look-back). Items
 // are staged in shared memory in digit order and written so that each digit's run is contiguous
 // and consecutive threads store consecutive words.
-template <int ITEMS>
+// With MASK, a 16-bit payload (the entry's tile mask) travels with each item as well.
+template <int ITEMS, bool MASK>
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const int64_t* count_dev,
+    const uint16_t* __restrict__ masks_in, uint32_t* __restrict__ keys_out,
+    uint32_t* __restrict__ vals_out, uint16_t* __restrict__ masks_out, const int64_t* count_dev,
     int64_t count_host, int64_t cap, int shift, const uint32_t* __restrict__ ghist,
     uint32_t* __restrict__ status, int* __restrict__ tile_counter, int32_t* __restrict__ err) {
   constexpr int W = kSortThreads / 32;
@@ -213,6 +416,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
   __shared__ uint32_t boff[kRadix];       // global start of this tile's run of each digit
   __shared__ uint32_t tmp[W];
   __shared__ uint32_t skey[kSortThreads * ITEMS], sval[kSortThreads * ITEMS];
+  __shared__ uint16_t smask[MASK ? kSortThreads * ITEMS : 1];
   __shared__ int s_tile;
   if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1);
   for (int k = threadIdx.x; k < W * kRadix; k += kSortThreads) (&wcount[0][0])[k] = 0;
@@ -224,6 +428,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
   uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
+  uint16_t msk[MASK ? ITEMS : 1];
   int dig[ITEMS];
   // all loads first, so that they are in flight together (the ranking below synchronizes the warp
   // between items)
@@ -233,6 +438,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const bool valid = i < count;
     key[r] = valid ? keys_in[i] : 0u;
     val[r] = valid ? vals_in[i] : 0u;
+    if (MASK) msk[MASK ? r : 0] = valid ? masks_in[i] : (uint16_t)0;
   }
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
@@ -273,6 +479,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
       const uint32_t p = dstart[dd] + wcount[warp][dd] + rank[r];
       skey[p] = key[r];
       sval[p] = val[r];
+      if (MASK) smask[MASK ? p : 0] = msk[MASK ? r : 0];
     }
   }
   __syncthreads();
@@ -281,8 +488,10 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const uint32_t k = skey[i];
     const int dd = (int)((k >> shift) & (kRadix - 1));
     const uint32_t pos = boff[dd] + (uint32_t)i - dstart[dd];
+    if (pos >= (uint32_t)count) continue;  // only after an expired look-back (offsets then short)
     keys_out[pos] = k;
     vals_out[pos] = sval[i];
+    if (MASK) masks_out[pos] = smask[MASK ? i : 0];
   }
 }
 
@@ -379,63 +588,80 @@ __global__ void __launch_bounds__(kSortThreads) k_depth_keys(
   }
 }
 
-// Exclusive prefix of the group counts of the Gaussians in depth order (single pass with
-// look-back); the last tile writes the total, the number of entries the frame needs.
-//
-// It also counts the entries of every group: each Gaussian adds its rectangle of groups to a 2D
-// difference array D over (GY + 1) x (GX + 1) cells (+1 at (gy0, gx0) and (gy1+1, gx1+1), -1 at
-// (gy0, gx1+1) and (gy1+1, gx0)), whose 2D prefix sum is the per-group count. A tile accumulates
-// D in shared memory and stores it to its own slice of `dslices` (no global atomics); if D does
-// not fit (`dslices` == NULL) the tile adds into the global D (`dglobal`) instead.
-__global__ void __launch_bounds__(kSortThreads) k_group_offsets(
+// Per visible Gaussian in depth order, its number of entries: the groups of its tile range that
+// hold a member tile. A warp takes 32 consecutive Gaussians (staged in shared memory) and spreads
+// their group rows over its lanes (lane k of a round takes row k of the warp's rows, locating its
+// Gaussian by a binary search over the prefix of row counts), so a large splat's rows are counted
+// in parallel. GW, GH > 0 fix the grouping at compile time (0: the run-time gw, gh).
+template <int GW, int GH>
+__global__ void __launch_bounds__(256) k_count_entries(
     const int64_t* __restrict__ visible, const uint32_t* __restrict__ order,
-    const int* __restrict__ radius,
-    const int4* __restrict__ rect, int gw, int gh, int GXp1, int cells,
-    uint64_t* __restrict__ offsets, int64_t* __restrict__ total, int32_t* __restrict__ dslices,
-    int32_t* __restrict__ dglobal, uint64_t* __restrict__ status, int* __restrict__ tile_counter,
-    int32_t* __restrict__ err) {
-  extern __shared__ int32_t sD[];
+    const int4* __restrict__ rect, const float2* __restrict__ mean2d,
+    const float4* __restrict__ conic_opacity, int gw_rt, int gh_rt, int use,
+    uint32_t* __restrict__ counts) {
+  const int gw = GW > 0 ? GW : gw_rt, gh = GH > 0 ? GH : gh_rt;
+  __shared__ WarpGauss sg_all[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = *visible;
+  if (s - lane >= n) return;  // warp-uniform
+  const WarpGauss w = warp_gauss(s, n, order, rect, mean2d, conic_opacity, gh, use != 0);
+  sg_all[warp][lane] = w;
+  __syncwarp();
+  const uint32_t incl = warp_incl_scan(w.rows);
+  const uint32_t excl = incl - w.rows;
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  uint32_t carry = 0;  // lane j: entries of Gaussian j counted so far
+  for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+    const uint32_t k = k0 + lane;
+    const int src = find_src(incl, k);
+    const uint32_t src_excl = __shfl_sync(0xffffffffu, excl, src);
+    uint32_t c = 0;
+    if (k < total) {
+      const WarpGauss& sg = sg_all[warp][src];
+      const int gy = sg.r.y / gh + (int)(k - src_excl);
+      c = row_group_count(row_runs(sg.g, use != 0, sg.r, gy, gh), gw);
+    }
+    const uint32_t S = warp_incl_scan(c);
+    const uint32_t lo_k = max(excl, k0), hi_k = min(incl, k0 + 32u);
+    const bool mine = w.rows > 0 && lo_k < hi_k;
+    const uint32_t sum = lanes_sum(S, mine ? lo_k : k0, mine ? hi_k : k0 + 1u, k0);
+    if (mine) carry += sum;
+  }
+  if (s < n) counts[s] = carry;
+}
+
+// Exclusive prefix of the entry counts in depth order (single pass with look-back); the last tile
+// writes the total, the number of entries the frame needs.
+__global__ void __launch_bounds__(kSortThreads) k_entry_offsets(
+    const int64_t* __restrict__ visible, const uint32_t* __restrict__ counts,
+    uint32_t* __restrict__ offsets, int64_t* __restrict__ total, uint64_t* __restrict__ status,
+    int* __restrict__ tile_counter, int32_t* __restrict__ err) {
   __shared__ uint64_t tmp[kSortThreads / 32];
   __shared__ uint64_t s_prefix;
   __shared__ int s_tile;
   if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1);
-  if (dslices)
-    for (int k = threadIdx.x; k < cells; k += kSortThreads) sD[k] = 0;
   __syncthreads();
   const int tile = s_tile;
   const int64_t n = *visible;
   const int64_t base = (int64_t)tile * kSortTile + (int64_t)threadIdx.x * kSortItems;
   if (n == 0 && tile == 0 && threadIdx.x == 0) *total = 0;
   if ((int64_t)tile * kSortTile >= n) return;
-  int32_t* D = dslices ? sD : dglobal;
   uint32_t c[kSortItems];
-  int4 rc[kSortItems];
   uint64_t sum = 0;
-  // loads first (the Gaussians in depth order are visible: compacted before the depth sort), so
-  // that the gathers of all items are in flight together
+  if (base + kSortItems <= n) {  // 16 consecutive counts: four 16-byte loads
+    const uint4* p = reinterpret_cast<const uint4*>(counts + base);
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    const int64_t s = base + k;
-    c[k] = s < n ? order[s] : 0xFFFFFFFFu;
-  }
-#pragma unroll
-  for (int k = 0; k < kSortItems; ++k)
-    rc[k] = c[k] != 0xFFFFFFFFu ? rect[c[k]] : make_int4(0, 0, 0, 0);
-#pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    uint32_t v = 0;
-    const int4 r = rc[k];
-    if (r.z > r.x) {
-      const int gx0 = r.x / gw, gx1 = (r.z - 1) / gw + 1, gy0 = r.y / gh, gy1 = (r.w - 1) / gh + 1;
-      v = (uint32_t)((gx1 - gx0) * (gy1 - gy0));
-      atomicAdd(&D[gy0 * GXp1 + gx0], 1);
-      atomicAdd(&D[gy0 * GXp1 + gx1], -1);
-      atomicAdd(&D[gy1 * GXp1 + gx0], -1);
-      atomicAdd(&D[gy1 * GXp1 + gx1], 1);
+    for (int k = 0; k < kSortItems / 4; ++k) {
+      const uint4 v = p[k];
+      c[4 * k] = v.x; c[4 * k + 1] = v.y; c[4 * k + 2] = v.z; c[4 * k + 3] = v.w;
     }
-    c[k] = v;
-    sum += v;
+  } else {
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) c[k] = base + k < n ? counts[base + k] : 0u;
   }
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) sum += c[k];
   uint64_t tile_total = 0;
   uint64_t run = block_excl_scan<uint64_t>(sum, tmp, &tile_total);
   if (threadIdx.x < 32) {
@@ -446,162 +672,110 @@ __global__ void __launch_bounds__(kSortThreads) k_group_offsets(
   run += s_prefix;
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
-    if (base + k < n) offsets[base + k] = run;
+    if (base + k < n) offsets[base + k] = (uint32_t)min(run, (uint64_t)0xFFFFFFFFu);
     run += c[k];
   }
   if (base < n && base + kSortItems >= n) *total = (int64_t)run;  // the thread holding item n-1
-  if (dslices) {
-    int32_t* out = dslices + (size_t)tile * cells;
-    for (int k = threadIdx.x; k < cells; k += kSortThreads) out[k] = sD[k];
-  }
 }
 
-// Sums the tiles' difference slices per cell into `dsum` (zeroed before): blockIdx.y takes every
-// gridDim.y-th tile, so many loads are in flight per cell.
-__global__ void k_group_reduce(const int32_t* __restrict__ dslices,
-                               const int64_t* __restrict__ visible, int cells,
-                               int32_t* __restrict__ dsum) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cells) return;
-  const int tiles = (int)((*visible + kSortTile - 1) / kSortTile);
-  int32_t v = 0;
-  for (int t = blockIdx.y; t < tiles; t += gridDim.y) v += dslices[(size_t)t * cells + c];
-  if (v) atomicAdd(&dsum[c], v);
-}
-
-// From the difference array: per-group entry counts (2D prefix sum, in place), the group ranges
-// (exclusive scan over row-major group ids) and the histograms of the group-id digits for the radix
-// passes. One block; does nothing if the frame needs more entries than the capacity.
-constexpr int kTableThreads = 1024;
-__global__ void __launch_bounds__(kTableThreads) k_group_table(
-    int32_t* __restrict__ Dg, int GX, int GY, int in_smem, const int64_t* __restrict__ total,
-    int64_t cap, int passes, uint32_t* __restrict__ ranges, uint32_t* __restrict__ ghist) {
-  extern __shared__ int32_t Ds[];
+// Emits the entries of each visible Gaussian, in depth order: for every group of its tile range
+// with a member tile, (group id, index, mask), the Gaussian's run starting at its offset. The warp
+// spreads its 32 Gaussians' group rows over its lanes as k_count_entries does (same arithmetic, so
+// the same counts); a lane writes its row's groups in order, at the row's position in the
+// Gaussian's run. The block also counts the group-id digits of its entries for the radix passes.
+template <int GW, int GH>
+__global__ void __launch_bounds__(256) k_emit(
+    const int64_t* __restrict__ visible, const uint32_t* __restrict__ order,
+    const int4* __restrict__ rect, const float2* __restrict__ mean2d,
+    const float4* __restrict__ conic_opacity, const uint32_t* __restrict__ offsets,
+    const int64_t* __restrict__ total_entries, int64_t cap, int gw_rt, int gh_rt, int GX, int use,
+    int passes, uint32_t* __restrict__ gkeys, uint32_t* __restrict__ vals,
+    uint16_t* __restrict__ masks, uint32_t* __restrict__ ghist) {
+  const int gw = GW > 0 ? GW : gw_rt, gh = GH > 0 ? GH : gh_rt;
   __shared__ uint32_t h[kMaxPasses * kRadix];
-  __shared__ uint32_t wsum[kTableThreads / 32];
-  __shared__ uint32_t s_carry;
-  if (*total > cap) return;
-  const int GXp1 = GX + 1;
-  int32_t* D = Dg;
-  if (in_smem) {  // work on a shared copy of the cells
-    for (int k = threadIdx.x; k < GXp1 * (GY + 1); k += kTableThreads) Ds[k] = Dg[k];
-    D = Ds;
-    __syncthreads();
-  }
-  for (int k = threadIdx.x; k < passes * kRadix; k += kTableThreads) h[k] = 0;
-  // prefix along x (one thread per row), then along y (one thread per column)
-  for (int y = threadIdx.x; y < GY; y += kTableThreads) {
-    int32_t run = 0;
-    for (int x = 0; x < GX; ++x) {
-      run += D[y * GXp1 + x];
-      D[y * GXp1 + x] = run;
-    }
-  }
+  __shared__ WarpGauss sg_all[8][32];
+  for (int k = threadIdx.x; k < passes * kRadix; k += blockDim.x) h[k] = 0;
   __syncthreads();
-  for (int x = threadIdx.x; x < GX; x += kTableThreads) {
-    int32_t run = 0;
-    for (int y = 0; y < GY; ++y) {
-      run += D[y * GXp1 + x];
-      D[y * GXp1 + x] = run;
-    }
-  }
-  __syncthreads();
-  // exclusive scan of the counts over g = y * GX + x, in chunks of the block's threads
-  if (threadIdx.x == 0) s_carry = 0;
-  const int G = GX * GY;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int g0 = 0; g0 < G; g0 += kTableThreads) {
-    const int g = g0 + threadIdx.x;
-    const uint32_t c = g < G ? (uint32_t)D[(g / GX) * GXp1 + (g % GX)] : 0u;
-    const uint32_t incl = warp_incl_scan(c);
-    __syncthreads();
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    uint32_t add = s_carry;
-    for (int w = 0; w < warp; ++w) add += wsum[w];
-    const uint32_t start = add + incl - c;
-    if (g < G) {
-      ranges[2 * g] = c ? start : 0u;
-      ranges[2 * g + 1] = c ? start + c : 0u;
-      for (int p = 0; p < passes; ++p)
-        if (c) atomicAdd(&h[p * kRadix + ((g >> (8 * p)) & 0xff)], c);
-    }
-    __syncthreads();
-    if (threadIdx.x == kTableThreads - 1) s_carry = start + c;
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < passes * kRadix; k += kTableThreads) ghist[k] = h[k];
-}
-
-// Duplicates each visible Gaussian once per overlapped group, in depth order. A warp handles 32
-// consecutive Gaussians; their entries are contiguous in the output, so the warp writes them
-// cooperatively (lane k of a round writes entry k), each lane locating its Gaussian by a binary
-// search over the warp's prefix of counts.
-__global__ void __launch_bounds__(256) k_emit(const int64_t* __restrict__ visible,
-                                              const uint32_t* __restrict__ order,
-                                              const int* __restrict__ radius,
-                                              const int4* __restrict__ rect,
-                                              const uint64_t* __restrict__ offsets,
-                                              const int64_t* __restrict__ total, int64_t cap,
-                                              int gw, int gh, int GX,
-                                              uint32_t* __restrict__ gkeys,
-                                              uint32_t* __restrict__ vals) {
-  const int lane = threadIdx.x & 31;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = *visible;
-  if (*total > cap || s - lane >= n) return;  // warp-uniform
-  {
-    uint32_t i = 0, cnt = 0;
-    int gx0 = 0, gy0 = 0, gwn = 1;
-    if (s < n) {
-      i = order[s];
-      if (radius[i] > 0) {
-        const int4 r = rect[i];
-        gx0 = r.x / gw;
-        gy0 = r.y / gh;
-        gwn = (r.z - 1) / gw - gx0 + 1;
-        cnt = (uint32_t)(gwn * ((r.w - 1) / gh - gy0 + 1));
-      }
-    }
-    const uint32_t incl = warp_incl_scan(cnt);
-    const uint32_t warp_total = __shfl_sync(0xffffffffu, incl, 31);
-    const uint64_t base = __shfl_sync(0xffffffffu, (s < n) ? offsets[s] : 0ull, 0);
-    for (uint32_t k0 = 0; k0 < warp_total; k0 += 32) {
+  if (*total_entries <= cap && s - lane < n) {  // warp-uniform
+    const WarpGauss w = warp_gauss(s, n, order, rect, mean2d, conic_opacity, gh, use != 0);
+    sg_all[warp][lane] = w;
+    __syncwarp();
+    const uint32_t base = s < n ? offsets[s] : 0u;
+    const uint32_t incl = warp_incl_scan(w.rows);
+    const uint32_t excl = incl - w.rows;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    uint32_t carry = 0;  // lane j: entries of Gaussian j written so far
+    for (uint32_t k0 = 0; k0 < total; k0 += 32) {
       const uint32_t k = k0 + lane;
-      // smallest source lane whose inclusive prefix exceeds k
-      int lo = 0;
+      const int src = find_src(incl, k);
+      const WarpGauss& sg = sg_all[warp][src];
+      const uint32_t src_excl = __shfl_sync(0xffffffffu, excl, src);
+      const uint32_t src_base = __shfl_sync(0xffffffffu, base, src);
+      const uint32_t src_carry = __shfl_sync(0xffffffffu, carry, src);
+      RowRuns q;
+      uint32_t c = 0;
+      int gy = 0;
+      if (k < total) {
+        gy = sg.r.y / gh + (int)(k - src_excl);
+        q = row_runs(sg.g, use != 0, sg.r, gy, gh);
+        c = row_group_count(q, gw);
+      }
+      const uint32_t S = warp_incl_scan(c);
+      // this row's position in its Gaussian's run: the Gaussian's earlier rounds, then its rows
+      // on lower lanes of this round
+      const uint32_t first = src_excl > k0 ? src_excl - k0 : 0u;
+      const uint32_t before_first = __shfl_sync(0xffffffffu, S, first > 0 ? (int)first - 1 : 0);
+      uint32_t pos = src_base + src_carry + (S - c) - (first > 0 ? before_first : 0u);
+      if (c > 0) {
+        int gmin = 0x7fffffff, gmax = -1;
 #pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const uint32_t v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
-        if (v <= k) lo += step;
+        for (int t = 0; t < TGS_MAX_GROUP; ++t)
+          if (q.lo[t] <= q.hi[t]) {
+            gmin = min(gmin, q.lo[t] / gw);
+            gmax = max(gmax, q.hi[t] / gw);
+          }
+        for (int gx = gmin; gx <= gmax; ++gx) {
+          const uint32_t m = row_group_mask(q, gx, gw);
+          if (!m) continue;
+          if (pos < (uint32_t)cap) {  // always, unless an expired look-back left the offsets short
+            const int gid = gy * GX + gx;
+            gkeys[pos] = (uint32_t)gid;
+            vals[pos] = sg.i;
+            masks[pos] = (uint16_t)m;
+            for (int p = 0; p < passes; ++p) atomicAdd(&h[p * kRadix + ((gid >> (8 * p)) & 0xff)], 1u);
+          }
+          ++pos;
+        }
       }
-      const uint32_t src_excl = __shfl_sync(0xffffffffu, incl - cnt, lo);
-      const uint32_t src_i = __shfl_sync(0xffffffffu, i, lo);
-      const int sx = __shfl_sync(0xffffffffu, gx0, lo), sy = __shfl_sync(0xffffffffu, gy0, lo);
-      const int sw = __shfl_sync(0xffffffffu, gwn, lo);
-      if (k < warp_total) {
-        const int li = (int)(k - src_excl);
-        // li / sw exactly: (li + 1/2) / sw is at least 1/(2 sw) away from an integer, far more
-        // than the float rounding of the quotient (li < 2^24, sw <= 4096)
-        const int qy = (int)(((float)li + 0.5f) * __frcp_rn((float)sw));
-        const int qx = li - qy * sw;
-        const uint64_t o = base + k;
-        gkeys[o] = (uint32_t)((sy + qy) * GX + (sx + qx));
-        vals[o] = src_i;
-      }
+      const uint32_t lo_k = max(excl, k0), hi_k = min(incl, k0 + 32u);
+      const bool mine = w.rows > 0 && lo_k < hi_k;
+      const uint32_t sum = lanes_sum(S, mine ? lo_k : k0, mine ? hi_k : k0 + 1u, k0);
+      if (mine) carry += sum;
     }
   }
+  __syncthreads();
+  for (int k = threadIdx.x; k < passes * kRadix; k += blockDim.x)
+    if (h[k]) atomicAdd(&ghist[k], h[k]);
 }
 
-// Masks and optional 64-bit keys of the sorted entries.
-__global__ void k_finalize(const int64_t* __restrict__ total, int64_t cap,
-                           const uint32_t* __restrict__ gkeys, const uint32_t* __restrict__ vals,
-                           const Finalize fin) {
+// Group ranges from the sorted group ids ([start, end) at the first and past the last entry of
+// each group; the others stay (0, 0)) and the optional 64-bit keys.
+__global__ void k_ranges(const int64_t* __restrict__ total, int64_t cap,
+                         const uint32_t* __restrict__ gkeys, const uint32_t* __restrict__ vals,
+                         const float* __restrict__ depth, uint32_t* __restrict__ ranges,
+                         uint64_t* __restrict__ keys64) {
   const int64_t E = *total;
   if (E > cap) return;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
-       e += (int64_t)gridDim.x * blockDim.x)
-    entry_outputs(fin, (uint32_t)e, gkeys[e], vals[e]);
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t g = gkeys[e];
+    if (e == 0 || gkeys[e - 1] != g) ranges[2 * (size_t)g] = (uint32_t)e;
+    if (e == E - 1 || gkeys[e + 1] != g) ranges[2 * (size_t)g + 1] = (uint32_t)(e + 1);
+    if (keys64) keys64[e] = ((uint64_t)g << 32) | __float_as_uint(depth[vals[e]]);
+  }
 }
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -609,15 +783,11 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Workspace: the ping-pong buffers, then one region that is cleared at the start of every call
 // (digit histograms, look-back status words, tile tickets).
 struct WsLayout {
-  size_t dkA, dkB, dvA, dvB, offs, gkA, gkB, gvB, dslices;
-  size_t zero_begin, hist_d, hist_g, stat_d, stat_g, stat_o, stat_c, tickets, dsum, visible,
-      zero_end;
-  int nb_c, nb_d, nb_g, nb_o, cells;
-  bool sliced;  // the difference array fits in shared memory: per-tile slices
+  size_t dkA, dkB, dvA, dvB, counts, offs, gkA, gkB, gvB, gmB;
+  size_t zero_begin, hist_d, hist_g, stat_d, stat_g, stat_o, stat_c, tickets, visible, zero_end;
+  int nb_c, nb_d, nb_g, nb_o;
   size_t total;
 };
-
-constexpr int kMaxSmemCells = 11776;  // 46 KB of int32 difference cells per tile
 
 int group_bits(int64_t G) {
   int bits = 0;
@@ -643,13 +813,12 @@ WsLayout layout(int64_t n, int64_t cap, int GX, int GY) {
   L.dkB = take(4 * (size_t)n);
   L.dvA = take(4 * (size_t)n);
   L.dvB = take(4 * (size_t)n);
-  L.offs = take(8 * (size_t)n);
+  L.counts = take(4 * (size_t)n);
+  L.offs = take(4 * (size_t)n);
   L.gkA = take(4 * (size_t)cap);
   L.gkB = take(4 * (size_t)cap);
   L.gvB = take(4 * (size_t)cap);
-  L.cells = (GX + 1) * (GY + 1);
-  L.sliced = L.cells <= kMaxSmemCells;
-  L.dslices = take(L.sliced ? 4 * (size_t)L.nb_o * L.cells : 0);
+  L.gmB = take(2 * (size_t)cap);
   L.zero_begin = off;
   L.hist_d = take(4 * 4 * kRadix);
   L.hist_g = take(4 * (size_t)kMaxPasses * kRadix);
@@ -659,7 +828,6 @@ WsLayout layout(int64_t n, int64_t cap, int GX, int GY) {
   L.stat_c = take(8 * (size_t)L.nb_c);
   L.tickets = take(4 * (4 + kMaxPasses + 2));
   L.visible = take(8);
-  L.dsum = take(4 * (size_t)L.cells);
   L.zero_end = off;
   L.total = off;
   return L;
@@ -672,7 +840,8 @@ size_t bin_sort_workspace_bytes(int64_t n, int64_t capacity, int GX, int GY) {
 }
 
 tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int height, int gw, int gh,
-                           void* ws, size_t ws_bytes, const tgs_bins& b, cudaStream_t st) {
+                           bool membership, void* ws, size_t ws_bytes, const tgs_bins& b,
+                           cudaStream_t st) {
   (void)ws_bytes;
   const int n = (int)n64;
   const int TX = div_up(width, kTile), TY = div_up(height, kTile);
@@ -685,25 +854,32 @@ tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int h
     return TGS_OK;
   }
   if (((uintptr_t)p.rect & 15)) return set_error("rect must be 16-byte aligned"), TGS_ERR_INVALID_ARGUMENT;
+  if (membership && (((uintptr_t)p.mean2d & 7) || ((uintptr_t)p.conic_opacity & 15) ||
+                     !p.mean2d || !p.conic_opacity))
+    return set_error("tile membership needs mean2d (8-byte aligned) and conic_opacity (16-byte "
+                     "aligned)"),
+           TGS_ERR_INVALID_ARGUMENT;
   const WsLayout L = layout(n64, cap, GX, GY);
   char* w = static_cast<char*>(ws);
   auto* dkA = reinterpret_cast<uint32_t*>(w + L.dkA);
   auto* dkB = reinterpret_cast<uint32_t*>(w + L.dkB);
   auto* dvA = reinterpret_cast<uint32_t*>(w + L.dvA);
   auto* dvB = reinterpret_cast<uint32_t*>(w + L.dvB);
-  auto* offs = reinterpret_cast<uint64_t*>(w + L.offs);
+  auto* counts = reinterpret_cast<uint32_t*>(w + L.counts);
+  auto* offs = reinterpret_cast<uint32_t*>(w + L.offs);
   auto* gkA = reinterpret_cast<uint32_t*>(w + L.gkA);
   auto* gkB = reinterpret_cast<uint32_t*>(w + L.gkB);
   auto* gvB = reinterpret_cast<uint32_t*>(w + L.gvB);
+  auto* gmB = reinterpret_cast<uint16_t*>(w + L.gmB);
   auto* hist_d = reinterpret_cast<uint32_t*>(w + L.hist_d);
   auto* hist_g = reinterpret_cast<uint32_t*>(w + L.hist_g);
   auto* stat_d = reinterpret_cast<uint32_t*>(w + L.stat_d);
   auto* stat_g = reinterpret_cast<uint32_t*>(w + L.stat_g);
   auto* stat_o = reinterpret_cast<uint64_t*>(w + L.stat_o);
   auto* tickets = reinterpret_cast<int*>(w + L.tickets);
-  auto* dslices = L.sliced ? reinterpret_cast<int32_t*>(w + L.dslices) : nullptr;
-  auto* dsum = reinterpret_cast<int32_t*>(w + L.dsum);
   const int4* rect = reinterpret_cast<const int4*>(p.rect);
+  const float2* m2 = reinterpret_cast<const float2*>(p.mean2d);
+  const float4* co = reinterpret_cast<const float4*>(p.conic_opacity);
   int32_t* err = device_error_word();
   TGS_CUDA(cudaMemsetAsync(w + L.zero_begin, 0, L.zero_end - L.zero_begin, st));
 
@@ -714,66 +890,63 @@ tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int h
   k_depth_keys<<<L.nb_c, kSortThreads, 0, st>>>(n, p.radius, p.depth, dkA, dvA, visible, hist_d,
                                                 stat_c, tickets + 4 + kMaxPasses + 1, err);
   TGS_CHECK_LAUNCH("k_depth_keys");
-  const Finalize fin{rect, p.depth, gw, gh, GX, b.masks, b.keys};
   for (int pass = 0; pass < 4; ++pass) {
     const bool odd = pass & 1;
-    k_onesweep<kDepthItems><<<L.nb_d, kSortThreads, 0, st>>>(
-        odd ? dkB : dkA, odd ? dvB : dvA, odd ? dkA : dkB, odd ? dvA : dvB, visible, 0, n,
-        8 * pass, hist_d + pass * kRadix, stat_d + (size_t)pass * L.nb_d * kRadix, tickets + pass,
-        err);
+    k_onesweep<kDepthItems, false><<<L.nb_d, kSortThreads, 0, st>>>(
+        odd ? dkB : dkA, odd ? dvB : dvA, nullptr, odd ? dkA : dkB, odd ? dvA : dvB, nullptr,
+        visible, 0, n, 8 * pass, hist_d + pass * kRadix, stat_d + (size_t)pass * L.nb_d * kRadix,
+        tickets + pass, err);
     TGS_CHECK_LAUNCH("k_onesweep");
   }
   const uint32_t* order = dvA;  // after an even number of passes
 
-  // 2. exclusive prefix of the group counts in depth order (total = needed entries) and the
-  //    per-group entry counts -> group ranges and group-id digit histograms
-  const int passes = div_up(group_bits(G), kRadixBits);
-  k_group_offsets<<<L.nb_o, kSortThreads, L.sliced ? 4 * L.cells : 0, st>>>(
-      visible, order, p.radius, rect, gw, gh, GX + 1, L.cells, offs, b.num_entries, dslices, dsum, stat_o,
-      tickets + 4 + kMaxPasses, err);
-  TGS_CHECK_LAUNCH("k_group_offsets");
+  // 2. entries per Gaussian in depth order and their exclusive prefix (total = needed entries)
+  // the visible count is not known on the host: one warp per 32 of all n Gaussians, the warps
+  // past the visible ones return at once
+  const int grp = gw * 10 + gh;
+  auto count_kernel = grp == 11 ? k_count_entries<1, 1> : grp == 22 ? k_count_entries<2, 2>
+                    : grp == 42 ? k_count_entries<4, 2> : grp == 24 ? k_count_entries<2, 4>
+                    : grp == 44 ? k_count_entries<4, 4> : k_count_entries<0, 0>;
+  count_kernel<<<div_up(n, 256), 256, 0, st>>>(visible, order, rect, m2, co, gw, gh,
+                                               membership ? 1 : 0, counts);
+  TGS_CHECK_LAUNCH("k_count_entries");
+  k_entry_offsets<<<L.nb_o, kSortThreads, 0, st>>>(visible, counts, offs, b.num_entries, stat_o,
+                                                   tickets + 4 + kMaxPasses, err);
+  TGS_CHECK_LAUNCH("k_entry_offsets");
   if (cap == 0) return TGS_OK;
-  if (L.sliced) {
-    const int tiles = div_up(n, kSortTile);
-    k_group_reduce<<<dim3(div_up(L.cells, 256), std::min(tiles, 32)), 256, 0, st>>>(
-        dslices, visible, L.cells, dsum);
-    TGS_CHECK_LAUNCH("k_group_reduce");
-  }
-  // the attribute is the kernel's largest request, not this call's: CUDA graphs captured for other
-  // image sizes launch the same function with their own sizes
-  const int table_smem = L.sliced ? 4 * L.cells : 0;
-  TGS_CUDA(cudaFuncSetAttribute(k_group_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                4 * kMaxSmemCells));
-  k_group_table<<<1, kTableThreads, table_smem, st>>>(
-      dsum, GX, GY, L.sliced ? 1 : 0, b.num_entries, cap, passes, b.ranges, hist_g);
-  TGS_CHECK_LAUNCH("k_group_table");
 
-  // 3. duplicate per overlapped group in depth order. The buffers are arranged so that the sorted
-  //    Gaussian indices end in b.vals after an odd or even number of radix passes.
+  // 3. emit (group id, index, mask) in depth order. The buffers are arranged so that the sorted
+  //    indices and masks end in b.vals and b.masks after an odd or even number of radix passes.
+  const int passes = div_up(group_bits(G), kRadixBits);
   uint32_t* ek = (passes & 1) ? gkB : gkA;
   uint32_t* ev = (passes & 1) ? gvB : b.vals;
+  uint16_t* em = (passes & 1) ? gmB : b.masks;
   uint32_t* ok = (passes & 1) ? gkA : gkB;
   uint32_t* ov = (passes & 1) ? b.vals : gvB;
-  k_emit<<<div_up(n, 256), 256, 0, st>>>(visible, order, p.radius, rect, offs, b.num_entries, cap, gw, gh,
-                                          GX, ek, ev);
+  uint16_t* om = (passes & 1) ? b.masks : gmB;
+  auto emit_kernel = grp == 11 ? k_emit<1, 1> : grp == 22 ? k_emit<2, 2> : grp == 42 ? k_emit<4, 2>
+                   : grp == 24 ? k_emit<2, 4> : grp == 44 ? k_emit<4, 4> : k_emit<0, 0>;
+  emit_kernel<<<div_up(n, 256), 256, 0, st>>>(visible, order, rect, m2, co, offs, b.num_entries, cap,
+                                               gw, gh, GX, membership ? 1 : 0, passes, ek, ev, em,
+                                               hist_g);
   TGS_CHECK_LAUNCH("k_emit");
 
-  // 4. stable sort by group id
+  // 4. stable sort by group id, carrying index and mask
   const uint32_t* gk = ek;
   for (int pass = 0; pass < passes; ++pass) {
     const bool odd = pass & 1;
-    k_onesweep<kGidItems><<<L.nb_g, kSortThreads, 0, st>>>(
-        odd ? ok : ek, odd ? ov : ev, odd ? ek : ok, odd ? ev : ov, b.num_entries, 0, cap,
-        8 * pass, hist_g + pass * kRadix, stat_g + (size_t)pass * L.nb_g * kRadix, tickets + 4 + pass,
-        err);
+    k_onesweep<kGidItems, true><<<L.nb_g, kSortThreads, 0, st>>>(
+        odd ? ok : ek, odd ? ov : ev, odd ? om : em, odd ? ek : ok, odd ? ev : ov, odd ? em : om,
+        b.num_entries, 0, cap, 8 * pass, hist_g + pass * kRadix,
+        stat_g + (size_t)pass * L.nb_g * kRadix, tickets + 4 + pass, err);
     TGS_CHECK_LAUNCH("k_onesweep");
     gk = odd ? ek : ok;
   }
 
-  // 5. masks and the optional 64-bit keys
-  const int fin_blocks = std::max(1, std::min(div_up(cap, 256), 152 * 16));
-  k_finalize<<<fin_blocks, 256, 0, st>>>(b.num_entries, cap, gk, b.vals, fin);
-  TGS_CHECK_LAUNCH("k_finalize");
+  // 5. group ranges and the optional 64-bit keys
+  const int rng_blocks = std::max(1, std::min(div_up(cap, 256), 152 * 16));
+  k_ranges<<<rng_blocks, 256, 0, st>>>(b.num_entries, cap, gk, b.vals, p.depth, b.ranges, b.keys);
+  TGS_CHECK_LAUNCH("k_ranges");
   return TGS_OK;
 }
 

@@ -369,7 +369,8 @@ tgs_status tgs_serve_create(const tgs_serve_config* config, tgs_server** out) {
       (c.precision != TGS_PRECISION_FP32 && c.precision != TGS_PRECISION_FP16_TC &&
        c.precision != TGS_PRECISION_BF16_TC) ||
       c.tiling.group_w < 1 || c.tiling.group_w > TGS_MAX_GROUP || c.tiling.group_h < 1 ||
-      c.tiling.group_h > TGS_MAX_GROUP || c.request_timeout_ms < 0)
+      c.tiling.group_h > TGS_MAX_GROUP || (c.tiling.flags & ~TGS_BIN_RANGE_ONLY) != 0 ||
+      c.request_timeout_ms < 0)
     return set_error("bad serving config"), TGS_ERR_INVALID_ARGUMENT;
   tgs_status s = tgs_check_device(c.device);
   if (s != TGS_OK) return s;

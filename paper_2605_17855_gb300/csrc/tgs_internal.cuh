@@ -46,7 +46,8 @@ tgs_status launch_preprocess(const tgs_scene& s, const tgs_camera& cam, const tg
                              cudaStream_t st);
 size_t bin_sort_workspace_bytes(int64_t n, int64_t capacity, int GX, int GY);
 tgs_status launch_bin_sort(const tgs_projected& p, int64_t n, int width, int height, int gw, int gh,
-                           void* ws, size_t ws_bytes, const tgs_bins& bins, cudaStream_t st);
+                           bool membership, void* ws, size_t ws_bytes, const tgs_bins& bins,
+                           cudaStream_t st);
 tgs_status launch_raster_fp32(const tgs_projected& p, const tgs_bins& b, int width, int height,
                               int gw, int gh, const tgs_raster_opts& o, float* out_rgb, float* out_T,
                               int32_t* n_contrib, cudaStream_t st);

@@ -28,7 +28,7 @@ class Bins(C.Structure):
 
 
 class Tiling(C.Structure):
-    _fields_ = [("group_w", C.c_int32), ("group_h", C.c_int32)]
+    _fields_ = [("group_w", C.c_int32), ("group_h", C.c_int32), ("flags", C.c_int32)]
 
 
 def main():
@@ -55,7 +55,8 @@ def main():
     torch.cuda.synchronize()
     frees.append(torch.cuda.mem_get_info(dev)[0])
     for (gw, gh) in ((2, 2), (2, 2), (4, 2)):  # the first one is the process's first library call
-        ob = oracle.bin_sort(pr.mean2d, pr.radius, pr.depth, cam.width, cam.height, gw, gh)
+        ob = oracle.bin_sort(pr.mean2d, pr.radius, pr.depth, cam.width, cam.height, gw, gh,
+                             conic=co[:, :3], opacity=co[:, 3])
         E = ob.num_entries
         GX = ((cam.width + 15) // 16 + gw - 1) // gw
         GY = ((cam.height + 15) // 16 + gh - 1) // gh

@@ -15,10 +15,7 @@ import oracle  # noqa: E402
 import paper_2605_17855_gb300 as tgs  # noqa: E402
 from paper_2605_17855_gb300 import scenes  # noqa: E402
 
-FP32_TOL = 1e-4
-TC_MAXABS = 2.0 / 255.0
-TC_PSNR = 45.0
-TC_MARGIN = 2e-4
+from parity_bars import check  # noqa: E402
 
 
 def _np(t):
@@ -43,7 +40,8 @@ def _check(scene, cam, tiling, precisions=("fp32", "fp16_tc", "bf16_tc")):
     co = _np(proj.conic_opacity).astype(np.float64)
     p = dict(mean2d=_np(proj.mean2d).astype(np.float64), conic=co[:, :3], opacity=co[:, 3],
              rgb=_np(proj.rgb).astype(np.float64), depth=_np(proj.depth), radius=_np(proj.radius))
-    ob = oracle.bin_sort(p["mean2d"], p["radius"], p["depth"], cam.width, cam.height, *tiling)
+    ob = oracle.bin_sort(p["mean2d"], p["radius"], p["depth"], cam.width, cam.height, *tiling,
+                         conic=p["conic"], opacity=p["opacity"])
     E = bins.entries
     assert E == ob.num_entries
     assert np.array_equal(_np(bins.vals[:E]).view(np.uint32), ob.vals)
@@ -57,17 +55,7 @@ def _check(scene, cam, tiling, precisions=("fp32", "fp16_tc", "bf16_tc")):
         torch.cuda.synchronize()
         assert tgs.last_device_error() == 0
         rgb, T, nc = _np(rgb), _np(T), _np(nc)
-        if prec == "fp32":
-            ok = img.margin > 1e-5
-            assert (~ok).mean() < 1e-3
-            assert np.abs(rgb - ref).max(axis=0)[ok].max() <= FP32_TOL
-            assert np.abs(T - img.T)[ok].max() <= FP32_TOL
-            assert np.array_equal(nc[ok], img.n_contrib[ok])
-        else:
-            assert oracle.psnr(rgb, ref) >= TC_PSNR, prec
-            ok = img.margin > TC_MARGIN
-            assert (~ok).mean() < 0.02
-            assert np.abs(rgb - ref).max(axis=0)[ok].max() <= TC_MAXABS, prec
+        check(prec, rgb, T, nc, ref, img.T, img.n_contrib, img.margin, (prec, tiling))
     return img
 
 
@@ -129,17 +117,19 @@ def test_minimal_splat_on_a_tile_corner():
         assert img.n_contrib.sum() > 0
 
 
-def test_many_groups_use_the_global_count_path():
-    # 4096 x 3000 at 1x1 tiles: 256 x 188 groups, more cells than the per-tile shared-memory arrays
-    # of the bin sort hold, so the group counts take the global-memory path
-    cam = scenes.identity_camera(4096, 3000, 60.0)
+@pytest.mark.parametrize("width,height", [(4096, 3000), (4608, 4096)])
+def test_many_groups(width, height):
+    # 1x1 tiles: 256 x 188 groups (16 group-id bits, two radix passes) and 288 x 256 groups (17
+    # bits, three passes: the sorted indices and masks reach the output after an odd number)
+    cam = scenes.identity_camera(width, height, 60.0)
     scene = scenes.box_scene(20000, seed=9, sh_degree=0, log_scale_mean=-4.5)
     ds = tgs.DeviceScene.from_host(scene)
     proj = tgs.preprocess(ds, cam)
     bins = tgs.bin_sort(proj, cam.width, cam.height, (1, 1))
     torch.cuda.synchronize()
+    co = _np(proj.conic_opacity).astype(np.float64)
     ob = oracle.bin_sort(_np(proj.mean2d).astype(np.float64), _np(proj.radius), _np(proj.depth),
-                         cam.width, cam.height, 1, 1)
+                         cam.width, cam.height, 1, 1, conic=co[:, :3], opacity=co[:, 3])
     E = bins.entries
     assert E == ob.num_entries and E > 20000
     assert np.array_equal(_np(bins.vals[:E]).view(np.uint32), ob.vals)
