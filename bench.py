@@ -38,9 +38,26 @@ METRIC = "rasterize Mpx/s & p99 frame ms, FP16-TC vs FP32-core, PSNR>=45dB vs or
 DTYPE = {"fp16_tc": "f16 products, f32 accumulate/blend", "bf16_tc": "bf16 products, f32 accumulate/blend",
          "fp32": "f32"}
 UNIT = "Mpx/s"
-MUFU_PER_SM_PER_CLK = 16  # ex2 results per SM per clock (special-function units)
-SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
+
+
+def _unit_peaks(device: int):
+    """Measured ex2 and FFMA rates of this GPU (the microbenchmark library) and its SM count."""
+    import ctypes as C
+
+    import torch
+    from paper_2605_17855_gb300 import build as _b
+    _b.build()
+    lib = C.CDLL(_b.MICROBENCH_LIB)
+    lib.tgs_microbench_peaks.restype = C.c_int
+    lib.tgs_microbench_peaks.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    scratch = torch.empty(8 * sms * 512, dtype=torch.float32, device="cuda")
+    ex2, ffma = C.c_double(0), C.c_double(0)
+    torch.cuda.synchronize()
+    if lib.tgs_microbench_peaks(C.c_void_p(scratch.data_ptr()), sms, C.byref(ex2), C.byref(ffma)) != 0:
+        raise RuntimeError("microbenchmark failed")
+    return {"sm_count": sms, "ex2_per_s": ex2.value, "ffma_per_s": ffma.value}
 
 
 def _peaks():
@@ -54,7 +71,7 @@ def _peaks():
 
 
 class ClockSampler:
-    """Samples nvidia-smi clocks and throttle reasons every 200 ms while running."""
+    """Samples nvidia-smi clocks and throttle reasons every 100 ms while running."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -70,7 +87,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (FileNotFoundError, OSError):
             self.proc = None
             return
@@ -456,8 +473,11 @@ def run_reference(args):
         vals.append(rec["value"])
     value = float(np.mean(vals))
     frame_ms = cam.width * cam.height / (value * 1e6) * 1e3
+    # ms_per_step is what a step ran (one bounded sample of a frame: full preprocess and bin sort,
+    # a sample of the blend); the rate is that sample's, extrapolated to the whole frame
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(8 * frame_ms, 3),
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * float(np.mean(times)), 3),
+           "frame_ms_extrapolated": round(frame_ms, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": _config(scene, cams, args),
            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": rec["cores"], "kind": "oracle",
@@ -472,6 +492,9 @@ def run_reference(args):
 # reported only while those sources are unchanged (the profile summary gives the command).
 TRAFFIC = {("k_raster_tc", "2x2"): {"bytes": 69140480,
                                    "sha1": "9d3a574d49c78af4a5ed253b234b696a44dbb839"}}
+# Pipe utilizations of the dominant kernel from the same kind of capture (ncu --set full), keyed by
+# the kernel; reported only while its sources hash to the recorded value.
+NCU_FRACTIONS = {}
 
 
 def _kernel_sources_sha1(kernel):
@@ -551,20 +574,31 @@ def main():
     H, W = cams[0].height, cams[0].width
     ds = tgs.DeviceScene.from_host(scene)
     stream = torch.cuda.current_stream()
-    # one pair of CUDA graphs per camera (preprocess + bin sort, rasterize): a frame is two launches
-    rend = tgs.Renderer(ds, cams, tiling, args.precision)
-    rend32 = tgs.Renderer(ds, cams, (1, 1), "fp32")  # the plain tile rasterizer, 1x1 tiles
-    # the same frames without the two-stream pipeline: the per-stage split and the rasterize
-    # kernel's own launch time (for the roofline) come from these
-    rend_serial = tgs.Renderer(ds, cams, tiling, args.precision, pipeline=False)
-    rend32_serial = tgs.Renderer(ds, cams, (1, 1), "fp32", pipeline=False)
-    # ablation: the same tensor-core path without the exact (Gaussian, tile) skip
-    rend_nc = tgs.Renderer(ds, cams, tiling, args.precision, cull=False) if args.precision != "fp32" else None
+    ncam = len(cams)
+    px_per_step = ncam * W * H
+    tc = args.precision != "fp32"
+    # The renderers: one pair of CUDA graphs per camera (preprocess + bin sort, rasterize), a frame
+    # is two launches. Pipelined (the next frame's preprocess + bin sort overlaps the previous
+    # frame's rasterize) for frame rates, unpipelined for the per-stage times and the rasterize
+    # kernel's own launch time. The plain FP32 CUDA-core rasterizer uses the original tile
+    # organization: 1x1 tiles and every tile of each Gaussian's AABB range.
+    R = {}
+
+    def make(key, tl, prec, membership=True, cull=True):
+        R[key] = (tgs.Renderer(ds, cams, tl, prec, membership=membership, cull=cull),
+                  tgs.Renderer(ds, cams, tl, prec, membership=membership, cull=cull, pipeline=False))
+
+    make("main", tiling, args.precision)
+    make("fp32_plain", (1, 1), "fp32", membership=False)
+    make("fp32_membership", (1, 1), "fp32")
+    if tc:
+        make("tc_range_skip", tiling, args.precision, membership=False)
+        make("tc_range_noskip", tiling, args.precision, membership=False, cull=False)
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
     def timed(r, steps, warmup):
         for _ in range(warmup):
-            for i in range(len(cams)):
+            for i in range(ncam):
                 r.render(i)
         torch.cuda.synchronize()
         if dist:
@@ -573,9 +607,10 @@ def main():
         evs = [[(ev(), ev(), ev()) for _ in cams] for _ in range(steps)]
         t0, t1 = ev(), ev()
         t0.record(stream)
-        torch.cuda.nvtx.range_push(f"timed_{r.precision}_{r.tiling[0]}x{r.tiling[1]}" + ("" if r.cull else "_noskip"))
+        torch.cuda.nvtx.range_push(f"timed_{r.precision}_{r.tiling[0]}x{r.tiling[1]}" + ("" if r.cull else "_noskip")
+                                   + ("" if r.membership else "_range"))
         for k in range(steps):
-            for i in range(len(cams)):
+            for i in range(ncam):
                 r.render(i, evs[k][i])
         r.join()
         torch.cuda.nvtx.range_pop()
@@ -594,93 +629,96 @@ def main():
         raster = np.array([m.elapsed_time(c) for row in evs for _, m, c in row])
         return total_ms, frames, prep, raster
 
+    # clocks are sampled over every timed phase (the headline loop alone is a fraction of a second)
     sampler = ClockSampler(local)
     sampler.start()
-    total_ms, frames_ms, prep_ms, raster_ms = timed(rend, args.steps, args.warmup)
+    total_ms, frames_ms, _, _ = timed(R["main"][0], args.steps, args.warmup)
     latency_ms = timed.latency
-    clocks = sampler.stop()
-    launches = int(args.steps * sum(rend.kernels_per_frame))
+    launches = int(args.steps * sum(R["main"][0].kernels_per_frame))
     ms_per_step = total_ms / args.steps
-    px_per_step = len(cams) * W * H
     value = whole_job_rate(ws, px_per_step, ms_per_step)
-    steps32 = max(3, args.steps // 2)
-    tot32, frames32, _, _ = timed(rend32, steps32, 3)
-    value32 = whole_job_rate(ws, px_per_step, tot32 / steps32)
-    # without the pipeline: the stage split and the kernels' own rasterize times
-    tots, _, prep_ms, raster_ms = timed(rend_serial, steps32, 3)
-    tot32s, _, prep32, raster32 = timed(rend32_serial, steps32, 3)
-    ablation = None
-    if rend_nc is not None:
-        totnc, framesnc, _, _ = timed(rend_nc, steps32, 3)
-        ablation = {"value": round(whole_job_rate(ws, px_per_step, totnc / steps32), 3), "unit": UNIT,
-                    "note": "fp16_tc without the exact per-(Gaussian, tile) skip (identical images)"}
-    # the other grouping / precision combinations of the comparison, each timed the same way
+    steps2 = max(3, args.steps // 2)
+    paths = {}
+    for key, (rp, rs) in R.items():
+        totp, framesp, _, _ = timed(rp, steps2, 3)
+        tots, _, prep, raster = timed(rs, steps2, 3)
+        if rp.overflowed() or rs.overflowed():
+            raise RuntimeError("bin capacity overflow during the benchmark")
+        paths[key] = {"value": round(whole_job_rate(ws, px_per_step, totp / steps2), 3), "unit": UNIT,
+                      "frame_ms_p99": round(float(np.percentile(framesp, 99)), 4),
+                      "value_without_pipeline": round(whole_job_rate(ws, px_per_step, tots / steps2), 3),
+                      "preprocess_plus_bin_sort_ms": round(float(prep.mean()), 4),
+                      "rasterize_ms": round(float(raster.mean()), 4)}
+    # the other grouping / precision combinations of the paper's comparison (Table 3, Table 5)
     variants = {}
-    for prec, tl in (("fp32", (2, 2)), ("fp16_tc", (1, 1))):
-        if (prec, tl) == (args.precision, tiling):
-            continue
-        rv = tgs.Renderer(ds, cams, tl, prec)
-        totv, framesv, _, _ = timed(rv, steps32, 3)
+    for prec, tl, memb in (("fp32", (2, 2), False), ("fp16_tc", (1, 1), True)):
+        rv = tgs.Renderer(ds, cams, tl, prec, membership=memb)
+        totv, framesv, _, _ = timed(rv, steps2, 3)
         if rv.overflowed():
             raise RuntimeError("bin capacity overflow during the benchmark")
-        variants[f"{prec}_{tl[0]}x{tl[1]}"] = {
-            "value": round(whole_job_rate(ws, px_per_step, totv / steps32), 3), "unit": UNIT,
+        variants[f"{prec}_{tl[0]}x{tl[1]}" + ("" if memb else "_range")] = {
+            "value": round(whole_job_rate(ws, px_per_step, totv / steps2), 3), "unit": UNIT,
             "frame_ms_p99": round(float(np.percentile(framesv, 99)), 4)}
         del rv
-    if rend.overflowed() or rend32.overflowed() or rend_serial.overflowed() or rend32_serial.overflowed():
-        raise RuntimeError("bin capacity overflow during the benchmark")
 
-    # split of the preprocess + bin sort stage for one frame (direct calls, untimed by the main loop)
+    # split of the preprocess + bin sort stage for one frame (direct calls)
+    rs = R["main"][1]
     e = [ev() for _ in range(3)]
     e[0].record(stream)
-    tgs.preprocess(ds, cams[0], out=rend_serial.proj)
+    tgs.preprocess(ds, cams[0], out=rs.proj)
     e[1].record(stream)
-    tgs.bin_sort(rend_serial.proj, W, H, tiling, bins=rend_serial.bins, sync=False)
+    tgs.bin_sort(rs.proj, W, H, tiling, bins=rs.bins, sync=False)
     e[2].record(stream)
     torch.cuda.synchronize()
-    stages = {"note": "frames without the two-stream pipeline (CUDA events between the stages)",
-              "value_without_pipeline": round(whole_job_rate(ws, px_per_step, tots / steps32), 3),
-              "preprocess_plus_bin_sort_ms": round(float(prep_ms.mean()), 4),
-              "rasterize_ms": round(float(raster_ms.mean()), 4),
+    stages = {"note": "the headline path without the two-stream pipeline (CUDA events between the stages)",
+              "value_without_pipeline": paths["main"]["value_without_pipeline"],
+              "preprocess_plus_bin_sort_ms": paths["main"]["preprocess_plus_bin_sort_ms"],
+              "rasterize_ms": paths["main"]["rasterize_ms"],
               "preprocess_ms_direct": round(e[0].elapsed_time(e[1]), 4),
               "bin_sort_ms_direct": round(e[1].elapsed_time(e[2]), 4)}
 
-    # algorithmic work of the dominant kernel per launch: the (pixel, entry) pairs evaluated before
-    # termination as the plain algorithm defines them (counted without the tile skip), the pairs
-    # the skip leaves, and the pairs that pass 1/255 (one exponential each)
-    cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
-    cnt_skip = torch.zeros(3, dtype=torch.int64, device="cuda")
-    entries = 0
+    # algorithmic work of the dominant kernel per launch. The plain algorithm's pairs: (pixel,
+    # entry) pairs evaluated before termination on the original tile lists (every tile of the AABB
+    # range, no skip); the pairs the headline path evaluates (membership lists, producer skip);
+    # the pairs that pass 1/255 (one exponential each).
+    cnt_plain = torch.zeros(3, dtype=torch.int64, device="cuda")
+    cnt_main = torch.zeros(3, dtype=torch.int64, device="cuda")
+    ent_plain = ent_main = 0
     for i, cam in enumerate(cams):
-        tgs.preprocess(ds, cam, out=rend_serial.proj)
-        tgs.bin_sort(rend_serial.proj, W, H, tiling, bins=rend_serial.bins, sync=False)
-        for c, cull in ((cnt, False), (cnt_skip, True)):
-            tgs.rasterize(rend_serial.proj, rend_serial.bins, W, H, args.precision,
-                          out=(rend_serial.out[i][0], rend_serial.out[i][1], None),
+        tgs.preprocess(ds, cam, out=rs.proj)
+        for c, memb, cull in ((cnt_plain, False, False), (cnt_main, True, True)):
+            bins = tgs.bin_sort(rs.proj, W, H, tiling, membership=memb)
+            tgs.rasterize(rs.proj, bins, W, H, args.precision, out=(rs.out[i][0], rs.out[i][1], None),
                           want_n_contrib=False, counters=c, cull=cull)
-        entries += int(rend_serial.bins.num_entries.item())
+            if memb:
+                ent_main += bins.entries
+            else:
+                ent_plain += bins.entries
     torch.cuda.synchronize()
-    pairs, exps, _ = [int(v) / len(cams) for v in cnt.cpu().tolist()]
-    pairs_after_skip = int(cnt_skip[0].item()) / len(cams)
-    slots = int(cnt_skip[2].item()) / len(cams)
-    entries /= len(cams)
+    pairs, exps, _ = [int(v) / ncam for v in cnt_plain.cpu().tolist()]
+    pairs_main, _, slots = [int(v) / ncam for v in cnt_main.cpu().tolist()]
 
-    # end to end through the public API: the scene copied host -> device from pinned memory and
-    # the 8 images device -> host into pinned memory, every step
+    # end to end through the C ABI: every step copies the scene host -> device from pinned memory,
+    # calls tgs_preprocess, tgs_bin_sort and tgs_rasterize per camera on one stream, and copies
+    # each image device -> host into pinned memory
     host = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32)).pin_memory()
             for k in ("means", "scales", "quats", "opacities", "sh")}
     host_imgs = [torch.empty((3, H, W), dtype=torch.float32).pin_memory() for _ in cams]
     h2d = sum(t.numel() * 4 for t in host.values())
     d2h = sum(t.numel() * 4 for t in host_imgs)
+    e_proj = tgs.Projected.empty(scene.n)
+    e_bins = tgs.allocate_bins(scene.n, int(max(ent_main, 1) / ncam * 1.5) + 4096, W, H, tiling, keys=False)
+    e_out = [(torch.empty((3, H, W), device="cuda"), torch.empty((H, W), device="cuda")) for _ in cams]
 
     def e2e_step():
         for k, t in host.items():
             getattr(ds, k).copy_(t, non_blocking=True)
-        for i in range(len(cams)):
-            rend.render(i)
-        rend.join()
-        for i in range(len(cams)):
-            host_imgs[i].copy_(rend.out[i][0], non_blocking=True)
+        for i, cam in enumerate(cams):
+            tgs.preprocess(ds, cam, out=e_proj)
+            tgs.bin_sort(e_proj, W, H, tiling, bins=e_bins, sync=False)
+            tgs.rasterize(e_proj, e_bins, W, H, args.precision, out=(e_out[i][0], e_out[i][1], None),
+                          want_n_contrib=False)
+            host_imgs[i].copy_(e_out[i][0], non_blocking=True)
 
     for _ in range(2):
         e2e_step()
@@ -692,30 +730,41 @@ def main():
         e2e_step()
     b.record(stream)
     torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if int(e_bins.num_entries.item()) > e_bins.capacity:
+        raise RuntimeError("bin capacity overflow in the end-to-end loop")
     e2e_ms = max_over_ranks(a.elapsed_time(b) / e2e_steps, dist, "cuda")
     e2e_value = whole_job_rate(ws, px_per_step, e2e_ms)
 
+    # roofline of the dominant kernel: the plain algorithm evaluates one ex2 per pair on the
+    # special-function units (the scarcest unit it uses), so its pair rate is bounded by the
+    # measured ex2 rate of this GPU
     peaks, peak_kind = _peaks()
+    unit_peaks = _unit_peaks(local)
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", SM_MAX_MHZ)
-    mufu_peak = SM_COUNT * MUFU_PER_SM_PER_CLK * peaks.get("sm_max_mhz", SM_MAX_MHZ) * 1e6 / 1e9
-    raster_avg_ms = float(raster_ms.mean())
-    # one evaluated pair costs the plain algorithm one ex2 on the special-function units, the
-    # scarcest unit it uses, so the pair rate is bounded by the MUFU ex2 rate
+    mufu_peak = unit_peaks["ex2_per_s"] / 1e9
+    raster_avg_ms = paths["main"]["rasterize_ms"]
     achieved = pairs / (raster_avg_ms * 1e-3) / 1e9
-    kernel = "k_raster_tc" if args.precision != "fp32" else "k_raster_fp32"
+    kernel = "k_raster_tc" if tc else "k_raster_fp32"
     roofline = {"bound": "alu", "kernel": kernel,
                 "achieved": round(achieved, 2), "peak": round(mufu_peak, 1), "unit": "Gpair/s",
                 "frac": round(achieved / mufu_peak, 4), "traffic": _traffic(kernel, args),
-                "peak_source": f"derived, of measured clock: {SM_COUNT} SMs x {MUFU_PER_SM_PER_CLK} MUFU ex2/clk x "
-                               f"{peaks.get('sm_max_mhz', SM_MAX_MHZ):.0f} MHz ({peak_kind} max SM clock); "
-                               "one ex2 per evaluated (pixel, entry) pair",
-                "work_per_launch": {"evaluated_pairs": pairs, "pairs_after_tile_skip": pairs_after_skip,
-                                    "pixel_slots_stepped": slots,
-                                    "exp_evaluations": exps, "group_entries": entries},
+                "peak_source": f"measured: ex2.approx.f32 microbenchmark on this GPU ({unit_peaks['sm_count']} SMs; "
+                               f"{unit_peaks['ex2_per_s'] / unit_peaks['sm_count'] / (sm_mhz * 1e6):.1f} ex2/clk/SM at "
+                               f"the {sm_mhz:.0f} MHz sampled during the timed phases); one ex2 per evaluated "
+                               "(pixel, entry) pair of the plain algorithm",
+                "work_per_launch": {"evaluated_pairs_plain": pairs, "evaluated_pairs_headline_path": pairs_main,
+                                    "pixel_slots_stepped": slots, "exp_evaluations": exps,
+                                    "group_entries": ent_main / ncam, "group_entries_plain": ent_plain / ncam},
                 "avg_launch_ms": round(raster_avg_ms, 4),
                 "exp_rate_gexps": round(exps / (raster_avg_ms * 1e-3) / 1e9, 2),
+                "ffma_peak_per_s": unit_peaks["ffma_per_s"],
                 "sm_mhz_during_timing": sm_mhz}
+    rec = NCU_FRACTIONS.get(kernel)
+    if rec is not None and rec["sha1"] == _kernel_sources_sha1(kernel):
+        roofline["ncu"] = {k: v for k, v in rec.items() if k != "sha1"}
 
+    plain = paths["fp32_plain"]
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
@@ -729,21 +778,30 @@ def main():
                                 "definition": "first kernel of the frame to its last (includes waiting for "
                                               "the previous frame's rasterize)"},
            "fps": round(1000.0 / float(frames_ms.mean()), 2),
-           "fp32_core_1x1": {"value": round(value32, 3), "unit": UNIT,
-                             "frame_ms_p99": round(float(np.percentile(frames32, 99)), 4),
-                             "value_without_pipeline": round(whole_job_rate(ws, px_per_step, tot32s / steps32), 3),
-                             "preprocess_plus_bin_sort_ms": round(float(prep32.mean()), 4),
-                             "rasterize_ms_mean": round(float(raster32.mean()), 4)},
-           "fp16_tc_without_tile_skip": ablation,
+           "fp32_core_1x1": dict(plain, note="the plain FP32 CUDA-core tile rasterizer: 1x1 tiles, every tile of "
+                                             "each Gaussian's AABB range (the original organization)"),
+           "ablations": {
+               "fp32_core_1x1_with_membership": dict(paths["fp32_membership"], note="FP32 CUDA cores on the same "
+                                                     "membership lists as the headline path (skip for skip)"),
+               **({"fp16_tc_range_lists": dict(paths["tc_range_skip"], note="tensor cores, AABB-range lists, the "
+                                               "rasterizer's own per-(Gaussian, tile) skip"),
+                   "fp16_tc_range_lists_no_skip": dict(paths["tc_range_noskip"], note="tensor cores, AABB-range lists, "
+                                                       "no skip at all (the paper's organization)")} if tc else {}),
+               "headline": {k: paths["main"][k] for k in ("value", "value_without_pipeline", "rasterize_ms",
+                                                          "preprocess_plus_bin_sort_ms")}},
            "variants": variants,
-           "speedup_vs_fp32_core": round(value / value32, 3),
-           "rasterize_speedup_vs_fp32_core": round(float(raster32.mean()) / raster_avg_ms, 3),
+           "speedup_vs_fp32_core": round(value / plain["value"], 3),
+           "rasterize_speedup_vs_fp32_core": round(plain["rasterize_ms"] / raster_avg_ms, 3),
+           "rasterize_speedup_skip_for_skip": round(paths["fp32_membership"]["rasterize_ms"] / raster_avg_ms, 3),
            "stages": stages,
-           "evals_per_s": round(pairs * len(cams) / (ms_per_step * 1e-3), 1),
+           "evals_per_s": round(pairs * ncam / (ms_per_step * 1e-3), 1),
            "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                   "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4)},
+                   "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4),
+                   "how": "per step: scene copied host -> device (pinned), tgs_preprocess, tgs_bin_sort and "
+                          "tgs_rasterize called per camera through the C ABI on one stream, each image copied "
+                          "device -> host (pinned)"},
            "gpu_launches": launches,
-           "kernels_per_frame": rend.kernels_per_frame[0],
+           "kernels_per_frame": R["main"][0].kernels_per_frame[0],
            "graphs": "one CUDA graph pair per camera (preprocess + bin sort, rasterize); the preprocess + "
                      "bin sort of a frame runs on a second stream of the highest priority, overlapping the previous "
                      "frame's rasterize",
@@ -753,6 +811,7 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         for k, t in host.items():  # restore the scene (the e2e loop copied the same values back)
             getattr(ds, k).copy_(t)
+        rend = R["main"][0]
         rgb, _ = rend.render(0)
         rend.join()
         torch.cuda.synchronize()

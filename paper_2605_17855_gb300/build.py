@@ -18,6 +18,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtgs.so")
+# the benchmark's microbenchmarks of the arithmetic units (separate from the tgs ABI)
+MICROBENCH_SRC = os.path.join(CSRC, "microbench", "peaks.cu")
+MICROBENCH_LIB = os.path.join(BUILD, "libtgs_microbench.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
@@ -39,10 +42,10 @@ def _deps():
 
 
 def needs_build() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(MICROBENCH_LIB):
         return True
-    t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(p) > t for p in _deps())
+    t = min(os.path.getmtime(LIB), os.path.getmtime(MICROBENCH_LIB))
+    return any(os.path.getmtime(p) > t for p in _deps() + [MICROBENCH_SRC])
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
@@ -60,8 +63,18 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
         return obj, r.stderr
 
+    def build_microbench():
+        tmp = MICROBENCH_LIB + f".{os.getpid()}.tmp"
+        r = subprocess.run([cc, *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+                            MICROBENCH_SRC, "-o", tmp], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {MICROBENCH_SRC}:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, MICROBENCH_LIB)
+
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
+        mb = ex.submit(build_microbench)
         results = list(ex.map(compile_one, sources()))
+        mb.result()
     if verbose or ptxas_info:
         for _, log in results:
             if log.strip():
