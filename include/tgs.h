@@ -212,6 +212,38 @@ tgs_status tgs_rasterize(const tgs_projected* proj, int64_t n, const tgs_bins* b
                          int32_t height, const tgs_tiling* tiling, const tgs_raster_opts* opts,
                          float* out_rgb, float* out_T, int32_t* n_contrib, void* stream);
 
+/* Batched tensor-core rasterization: several frames -- of different scenes, resolutions and
+ * bins -- rendered by ONE persistent launch (Section 4.4.2's per-group CTA loop over the union of
+ * the frames' tile groups; the paper renders one frame at a time and has no counterpart). The work
+ * items are the (frame, tile group) pairs; a CTA takes the next item from a device counter until
+ * none is left. Each frame's pixels are exactly those tgs_rasterize gives for the same inputs.
+ * If frames[f].ready != NULL, frame f's items start only once *ready >= ready_value (device int32,
+ * e.g. set by the stream that bins the frame): each CTA waits for it at most wait_limit_ns
+ * (<= 0: 2 s); on expiry *status (if non-NULL) is set to TGS_ERR_TIMEOUT and the frame's items
+ * are skipped, their pixels left unwritten. status (device int32, optional) is written only on
+ * failure: the caller sets it to TGS_OK before the call. Precision FP16_TC or BF16_TC (FP32:
+ * TGS_ERR_INVALID_ARGUMENT; use tgs_rasterize); opts->counters must be NULL. `workspace` is
+ * TGS_BATCH_WORKSPACE_BYTES of device memory (the work counter; cleared by the call), owned by the
+ * caller and not shared by overlapping calls. Errors: INVALID_ARGUMENT for count outside
+ * 1..TGS_BATCH_MAX_FRAMES or a bad frame (reported with its index). */
+#define TGS_BATCH_MAX_FRAMES 32
+#define TGS_BATCH_WORKSPACE_BYTES 256
+typedef struct {
+  const tgs_projected* proj; /* the frame's projected Gaussians (as for tgs_rasterize) */
+  int64_t n;
+  const tgs_bins* bins;      /* its bins, built with the batch's tiling */
+  int32_t width, height;
+  float* out_rgb;            /* device [3,H,W] */
+  float* out_T;              /* device [H,W] */
+  const int32_t* ready;      /* optional device readiness flag */
+  int32_t ready_value;
+  int32_t* status;           /* optional device status word */
+} tgs_frame;
+
+tgs_status tgs_rasterize_batch(const tgs_frame* frames, int32_t count, const tgs_tiling* tiling,
+                               const tgs_raster_opts* opts, int64_t wait_limit_ns, void* workspace,
+                               void* stream);
+
 /* Backward of tgs_rasterize for L = sum(out_rgb * grad_rgb): replays each pixel's list backwards
  * from n_contrib, recovering T_i = T_{i+1} / (1 - alpha_i) from the stored final T. Outputs are
  * overwritten (the call zeroes them first): g_mean2d [n,2] (d/d mu' in pixels), g_conic_opacity

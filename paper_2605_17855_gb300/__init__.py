@@ -81,6 +81,16 @@ class _RasterOpts(C.Structure):
 RASTER_NO_CULL = 1
 
 
+class _Frame(C.Structure):
+    _fields_ = [("proj", C.POINTER(_Projected)), ("n", C.c_int64), ("bins", C.POINTER(_Bins)),
+                ("width", C.c_int32), ("height", C.c_int32), ("out_rgb", C.c_void_p), ("out_T", C.c_void_p),
+                ("ready", C.c_void_p), ("ready_value", C.c_int32), ("status", C.c_void_p)]
+
+
+BATCH_MAX_FRAMES = 32
+BATCH_WORKSPACE_BYTES = 256
+
+
 _P = C.c_void_p
 _lib = None
 _lock = threading.Lock()
@@ -122,6 +132,8 @@ SIGNATURES = {
                                         C.POINTER(_Tiling), C.POINTER(_Bins), C.POINTER(C.c_int64), _P]),
     "tgs_rasterize": (C.c_int32, [C.POINTER(_Projected), C.c_int64, C.POINTER(_Bins), C.c_int32, C.c_int32,
                                   C.POINTER(_Tiling), C.POINTER(_RasterOpts), _P, _P, _P, _P]),
+    "tgs_rasterize_batch": (C.c_int32, [C.POINTER(_Frame), C.c_int32, C.POINTER(_Tiling), C.POINTER(_RasterOpts),
+                                        C.c_int64, _P, _P]),
     "tgs_rasterize_backward": (C.c_int32, [C.POINTER(_Projected), C.c_int64, C.POINTER(_Bins), C.c_int32,
                                            C.c_int32, C.POINTER(_Tiling), C.POINTER(_RasterOpts), _P, _P,
                                            _P, _P, _P, _P, _P]),
@@ -378,6 +390,46 @@ def rasterize(proj: Projected, bins: Bins, width, height, precision="fp16_tc", b
     _check(lib.tgs_rasterize(C.byref(proj.struct()), proj.n, C.byref(bins.struct()), int(width), int(height),
                              C.byref(t), C.byref(o), _ptr(rgb), _ptr(T), _ptr(nc), _stream(stream)))
     return rgb, T, nc
+
+
+@dataclass
+class BatchFrame:
+    """One frame of rasterize_batch: its projected Gaussians and bins, and where its image goes.
+    ready / status are optional device int32 tensors of one element (readiness flag, status word)."""
+    proj: Projected
+    bins: Bins
+    width: int
+    height: int
+    out_rgb: "object"        # [3,H,W] float32 (device)
+    out_T: "object"          # [H,W] float32 (device)
+    ready: "object" = None
+    ready_value: int = 1
+    status: "object" = None
+
+
+def rasterize_batch(frames, tiling=(2, 2), precision="fp16_tc", bg=(0.0, 0.0, 0.0), wait_limit_ns=0,
+                    workspace=None, stream=None, cull=True):
+    """tgs_rasterize_batch: every frame (of any scene and resolution) in one persistent tensor-core
+    launch. Returns the workspace tensor (reusable by later calls on the same stream)."""
+    lib = load()
+    if not frames:
+        raise ValueError("no frames")
+    dev = frames[0].proj.mean2d.device
+    if workspace is None:
+        workspace = torch.empty(BATCH_WORKSPACE_BYTES, dtype=torch.uint8, device=dev)
+    keep = []
+    arr = (_Frame * len(frames))()
+    for k, f in enumerate(frames):
+        ps, bs = f.proj.struct(), f.bins.struct()
+        keep += [ps, bs]
+        arr[k] = _Frame(C.pointer(ps), f.proj.n, C.pointer(bs), int(f.width), int(f.height), _ptr(f.out_rgb),
+                        _ptr(f.out_T), _ptr(f.ready), int(f.ready_value), _ptr(f.status))
+    o = _RasterOpts(PRECISION[precision], 0 if cull else RASTER_NO_CULL,
+                    (C.c_float * 3)(*[float(v) for v in bg]), None)
+    t = _tiling(tiling)
+    _check(lib.tgs_rasterize_batch(arr, len(frames), C.byref(t), C.byref(o), int(wait_limit_ns),
+                                   _ptr(workspace), _stream(stream)))
+    return workspace
 
 
 def rasterize_backward(proj: Projected, bins: Bins, width, height, T, n_contrib, grad_rgb,

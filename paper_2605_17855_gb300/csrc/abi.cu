@@ -222,6 +222,39 @@ tgs_status tgs_rasterize(const tgs_projected* proj, int64_t n, const tgs_bins* b
   }
 }
 
+tgs_status tgs_rasterize_batch(const tgs_frame* frames, int32_t count, const tgs_tiling* tiling,
+                               const tgs_raster_opts* opts, int64_t wait_limit_ns, void* workspace,
+                               void* stream) {
+  g_msg[0] = 0;
+  if (!frames || !opts || !valid_tiling(tiling) || count < 1 || count > TGS_BATCH_MAX_FRAMES)
+    return set_error("bad argument (count %d, 1..%d frames)", count, TGS_BATCH_MAX_FRAMES),
+           TGS_ERR_INVALID_ARGUMENT;
+  if (opts->precision != TGS_PRECISION_FP16_TC && opts->precision != TGS_PRECISION_BF16_TC)
+    return set_error("batched rasterization runs on the tensor cores (precision %d)", opts->precision),
+           TGS_ERR_INVALID_ARGUMENT;
+  if (opts->counters) return set_error("batched rasterization collects no counters"), TGS_ERR_INVALID_ARGUMENT;
+  if (!workspace || ((uintptr_t)workspace & 3))
+    return set_error("workspace of TGS_BATCH_WORKSPACE_BYTES device bytes needed"), TGS_ERR_INVALID_ARGUMENT;
+  RasterFrame rf[TGS_BATCH_MAX_FRAMES];
+  for (int f = 0; f < count; ++f) {
+    const tgs_frame& fr = frames[f];
+    const tgs_status s = check_raster_args(fr.proj, fr.n, fr.bins, fr.width, fr.height, tiling, opts);
+    if (s != TGS_OK) {
+      char m[512];
+      snprintf(m, sizeof m, "%s", g_msg);
+      return set_error("frame %d: %s", f, m), s;
+    }
+    if (!fr.out_rgb || !fr.out_T) return set_error("frame %d: null output", f), TGS_ERR_INVALID_ARGUMENT;
+    rf[f] = RasterFrame{fr.proj, fr.bins, fr.width, fr.height, fr.out_rgb, fr.out_T, fr.ready,
+                        fr.ready_value, fr.status};
+  }
+  tgs_status s = require_current_sm103();
+  if (s != TGS_OK) return s;
+  const uint64_t wait_ns = wait_limit_ns > 0 ? (uint64_t)wait_limit_ns : 2000000000ull;
+  return launch_raster_tc_batch(rf, count, tiling->group_w, tiling->group_h, *opts,
+                                static_cast<int*>(workspace), wait_ns, (cudaStream_t)stream);
+}
+
 tgs_status tgs_rasterize_backward(const tgs_projected* proj, int64_t n, const tgs_bins* bins,
                                   int32_t width, int32_t height, const tgs_tiling* tiling,
                                   const tgs_raster_opts* opts, const float* out_T,

@@ -12,4 +12,12 @@ tgs_status launch_raster_tc(const tgs_projected& p, const tgs_bins& b, int width
   return launch_raster_tc_typed<false>(p, b, width, height, gw, gh, o, out_rgb, out_T, n_contrib, st);
 }
 
+tgs_status launch_raster_tc_batch(const RasterFrame* frames, int count, int gw, int gh,
+                                  const tgs_raster_opts& o, int* next_item, uint64_t wait_ns,
+                                  cudaStream_t st) {
+  if (o.precision == TGS_PRECISION_BF16_TC)
+    return launch_raster_tc_batch_bf16(frames, count, gw, gh, o, next_item, wait_ns, st);
+  return launch_raster_tc_batch_typed<false>(frames, count, gw, gh, o, next_item, wait_ns, st);
+}
+
 }  // namespace tgs

@@ -11,4 +11,10 @@ tgs_status launch_raster_tc_bf16(const tgs_projected& p, const tgs_bins& b, int 
   return launch_raster_tc_typed<true>(p, b, width, height, gw, gh, o, out_rgb, out_T, n_contrib, st);
 }
 
+tgs_status launch_raster_tc_batch_bf16(const RasterFrame* frames, int count, int gw, int gh,
+                                       const tgs_raster_opts& o, int* next_item, uint64_t wait_ns,
+                                       cudaStream_t st) {
+  return launch_raster_tc_batch_typed<true>(frames, count, gw, gh, o, next_item, wait_ns, st);
+}
+
 }  // namespace tgs

@@ -297,25 +297,11 @@ __device__ __forceinline__ void blend_granule(const uint32_t (&d)[2 * W], int g,
   }
 }
 
-template <int GW, int GH, int NWG, int NPROD, int NST, bool BF, bool COUNT, bool NC>
-__global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NST)
-    k_raster_tc(const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ vals,
-                const uint16_t* __restrict__ masks, const float2* __restrict__ mean2d,
-                const float4* __restrict__ conic_opacity, const float* __restrict__ rgb, int width,
-                int height, int GX, float3 bg, float* __restrict__ out_rgb,
-                float* __restrict__ out_T, int* __restrict__ n_contrib,
-                unsigned long long* __restrict__ counters, int32_t* __restrict__ err, int cull) {
-  using C = Cfg<GW, GH, NWG, NPROD, NST>;
-  constexpr int TILES = C::kTiles;
-  constexpr int SLOTS = C::kSlots;
-  constexpr int KB = BF ? 2 : 1;  // K blocks of 16: FP16 hi|lo, or BF16 hi|mid then lo
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
-  auto& S = *reinterpret_cast<Smem<TILES, SLOTS, KB>*>(smem_raw);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gid = blockIdx.x;
-  const int gx = gid % GX, gy = gid / GX;
+// ---- set-up helpers shared by the single-frame and the batched kernel ------------------------
 
-  // ---- set-up: feature operand A, barriers, tensor memory -------------------------------------
+// The constant feature operand A (exact integers in FP16 and BF16), written by the whole CTA.
+template <int TILES, int SLOTS, int KB, bool BF>
+__device__ __forceinline__ void write_feature_operand(Smem<TILES, SLOTS, KB>& S) {
   for (int m = threadIdx.x; m < 256; m += blockDim.x) {
     const int h = m >> 7, row = m & 127;
     int lx, ly;
@@ -339,31 +325,59 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
       *reinterpret_cast<uint4*>(rowq + kLBO) = c1;
     }
   }
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < SLOTS; ++s) {
-      mbar_init(&S.full[s], 1);
-      mbar_init(&S.empty[s], C::kEpiWarps + 1);
-    }
-    for (int s = 0; s < 2; ++s) {
-      mbar_init(&S.tfull[s], 1);
-      mbar_init(&S.tempty[s], C::kEpiWarps);
-    }
-    mbar_init(&S.drain, 1);
-    S.abort = 0;
-    S.stop = 0;
-    S.end_job = -1;
-    S.done_warps = 0;
-    fence_mbarrier_init();
+}
+
+// Barriers and per-group flags in their initial state (thread 0 only).
+template <class C, int TILES, int SLOTS, int KB>
+__device__ __forceinline__ void init_group_state(Smem<TILES, SLOTS, KB>& S) {
+  for (int s = 0; s < SLOTS; ++s) {
+    mbar_init(&S.full[s], 1);
+    mbar_init(&S.empty[s], C::kEpiWarps + 1);
   }
-  if (warp == C::kMmaWarp) {
-    tmem_alloc(&S.tmem_base, C::kTmemCols);
-    tmem_relinquish();
+  for (int s = 0; s < 2; ++s) {
+    mbar_init(&S.tfull[s], 1);
+    mbar_init(&S.tempty[s], C::kEpiWarps);
   }
-  fence_proxy_async_smem();
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = S.tmem_base;
+  mbar_init(&S.drain, 1);
+  S.abort = 0;
+  S.stop = 0;
+  S.end_job = -1;
+  S.done_warps = 0;
+  fence_mbarrier_init();
+}
+
+// The barriers invalidated, so that init_group_state may use their memory again (thread 0, after a
+// CTA barrier that follows the drain of every tensor-core operation).
+template <int TILES, int SLOTS, int KB>
+__device__ __forceinline__ void inval_group_state(Smem<TILES, SLOTS, KB>& S) {
+  for (int s = 0; s < SLOTS; ++s) {
+    mbar_inval(&S.full[s]);
+    mbar_inval(&S.empty[s]);
+  }
+  for (int s = 0; s < 2; ++s) {
+    mbar_inval(&S.tfull[s]);
+    mbar_inval(&S.tempty[s]);
+  }
+  mbar_inval(&S.drain);
+}
+
+// One tile group of one frame: producers, MMA thread and epilogue warpgroups (all warps of the CTA
+// call it). Tensor memory is allocated, the feature operand written and the group state
+// initialized by the caller.
+template <int GW, int GH, int NWG, int NPROD, int NST, bool BF, bool COUNT, bool NC>
+__device__ __forceinline__ void raster_group(
+    Smem<GW * GH, Cfg<GW, GH, NWG, NPROD, NST>::kSlots, BF ? 2 : 1>& S, const uint32_t tmem,
+    const int gid, const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ vals,
+    const uint16_t* __restrict__ masks, const float2* __restrict__ mean2d,
+    const float4* __restrict__ conic_opacity, const float* __restrict__ rgb, int width, int height,
+    int GX, float3 bg, float* __restrict__ out_rgb, float* __restrict__ out_T,
+    int* __restrict__ n_contrib, unsigned long long* __restrict__ counters,
+    int32_t* __restrict__ err, int cull) {
+  using C = Cfg<GW, GH, NWG, NPROD, NST>;
+  constexpr int TILES = C::kTiles;
+  constexpr int KB = BF ? 2 : 1;  // K blocks of 16: FP16 hi|lo, or BF16 hi|mid then lo
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gx = gid % GX, gy = gid / GX;
   volatile int* abort_flag = &S.abort;
   volatile int* stop_flag = &S.stop;
 
@@ -806,11 +820,154 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
     }
   }
 
+}
+
+template <int GW, int GH, int NWG, int NPROD, int NST, bool BF, bool COUNT, bool NC>
+__global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NST)
+    k_raster_tc(const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ vals,
+                const uint16_t* __restrict__ masks, const float2* __restrict__ mean2d,
+                const float4* __restrict__ conic_opacity, const float* __restrict__ rgb, int width,
+                int height, int GX, float3 bg, float* __restrict__ out_rgb,
+                float* __restrict__ out_T, int* __restrict__ n_contrib,
+                unsigned long long* __restrict__ counters, int32_t* __restrict__ err, int cull) {
+  using C = Cfg<GW, GH, NWG, NPROD, NST>;
+  constexpr int TILES = C::kTiles;
+  constexpr int SLOTS = C::kSlots;
+  constexpr int KB = BF ? 2 : 1;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  auto& S = *reinterpret_cast<Smem<TILES, SLOTS, KB>*>(smem_raw);
+  const int warp = threadIdx.x >> 5;
+  // ---- set-up: feature operand A, barriers, tensor memory -------------------------------------
+  write_feature_operand<TILES, SLOTS, KB, BF>(S);
+  if (threadIdx.x == 0) init_group_state<C>(S);
+  if (warp == C::kMmaWarp) {
+    tmem_alloc(&S.tmem_base, C::kTmemCols);
+    tmem_relinquish();
+  }
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  raster_group<GW, GH, NWG, NPROD, NST, BF, COUNT, NC>(
+      S, S.tmem_base, blockIdx.x, ranges, vals, masks, mean2d, conic_opacity, rgb, width, height, GX,
+      bg, out_rgb, out_T, n_contrib, counters, err, cull);
   // ---- teardown -----------------------------------------------------------------------------
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == C::kMmaWarp) tmem_dealloc(tmem, C::kTmemCols);
+  if (warp == C::kMmaWarp) tmem_dealloc(S.tmem_base, C::kTmemCols);
+}
+
+// ---- batched rasterization: several frames in one persistent launch ---------------------------
+// The work items are the (frame, tile group) pairs of all frames, numbered frame by frame. Each
+// CTA takes the next item from a device counter until none is left, so frames of any size and
+// resolution share the GPU in one launch; between items the CTA drains its tensor-core work and
+// re-initializes its barriers. Before the first item of a frame is rendered, the frame's readiness
+// flag (if any) must have reached its value: the CTA waits for it at most `wait_ns`; on expiry the
+// frame's status word becomes TGS_ERR_TIMEOUT and its items are skipped (their pixels are not
+// written), and items of a frame already marked failed are skipped at once.
+constexpr int kMaxBatchFrames = 32;
+
+struct BatchFrame {
+  const uint32_t* ranges;
+  const uint32_t* vals;
+  const uint16_t* masks;
+  const float2* mean2d;
+  const float4* conic_opacity;
+  const float* rgb;
+  float* out_rgb;
+  float* out_T;
+  const int32_t* ready;  // may be NULL
+  int32_t* status;       // may be NULL
+  int32_t ready_value;
+  int32_t width, height, GX;
+};
+
+struct BatchArgs {
+  BatchFrame f[kMaxBatchFrames];
+  int32_t start[kMaxBatchFrames + 1];  // first work item of each frame; start[count] = total
+  int32_t count;
+};
+
+// Waits until *flag >= value, at most limit_ns; true when it got there.
+__device__ __forceinline__ bool wait_flag(const int32_t* flag, int32_t value, uint64_t limit_ns) {
+  const volatile int32_t* f = flag;
+  if (*f >= value) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    __nanosleep(2000);
+    if (*f >= value) return true;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+template <int GW, int GH, int NWG, int NPROD, int NST, bool BF>
+__global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NST)
+    k_raster_tc_batch(const __grid_constant__ BatchArgs B, int* __restrict__ next_item, float3 bg,
+                      int32_t* __restrict__ err, int cull, uint64_t wait_ns) {
+  using C = Cfg<GW, GH, NWG, NPROD, NST>;
+  constexpr int TILES = C::kTiles;
+  constexpr int SLOTS = C::kSlots;
+  constexpr int KB = BF ? 2 : 1;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  auto& S = *reinterpret_cast<Smem<TILES, SLOTS, KB>*>(smem_raw);
+  __shared__ int s_item, s_frame, s_run;
+  const int warp = threadIdx.x >> 5;
+  write_feature_operand<TILES, SLOTS, KB, BF>(S);
+  if (threadIdx.x == 0) init_group_state<C>(S);
+  if (warp == C::kMmaWarp) {
+    tmem_alloc(&S.tmem_base, C::kTmemCols);
+    tmem_relinquish();
+  }
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const int total = B.start[B.count];
+  while (true) {
+    if (threadIdx.x == 0) {
+      const int item = atomicAdd(next_item, 1);
+      int f = 0;
+      while (f + 1 < B.count && B.start[f + 1] <= item) ++f;
+      int run = item < total ? 1 : 0;
+      if (run) {
+        const BatchFrame& fr = B.f[f];
+        if (fr.status && *reinterpret_cast<volatile int32_t*>(fr.status) != TGS_OK) {
+          run = 0;  // the frame has already failed
+        } else if (fr.ready && !wait_flag(fr.ready, fr.ready_value, wait_ns)) {
+          run = 0;
+          if (fr.status) atomicExch(fr.status, TGS_ERR_TIMEOUT);
+        }
+      }
+      s_item = item;
+      s_frame = f;
+      s_run = run;
+    }
+    __syncthreads();
+    const int item = s_item, f = s_frame;
+    if (item >= total) break;
+    if (s_run) {
+      const BatchFrame& fr = B.f[f];
+      raster_group<GW, GH, NWG, NPROD, NST, BF, false, false>(
+          S, S.tmem_base, item - B.start[f], fr.ranges, fr.vals, fr.masks, fr.mean2d,
+          fr.conic_opacity, fr.rgb, fr.width, fr.height, fr.GX, bg, fr.out_rgb, fr.out_T, nullptr,
+          nullptr, err, cull);
+    }
+    // every warp is done with the item and the MMA thread has drained its tensor-core work
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (S.abort) break;  // a bounded wait expired: this CTA stops (uniform: read after the barrier)
+    if (threadIdx.x == 0 && s_run) {
+      inval_group_state(S);
+      init_group_state<C>(S);
+    }
+    __syncthreads();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == C::kMmaWarp) tmem_dealloc(S.tmem_base, C::kTmemCols);
 }
 
 template <bool BF, int GW, int GH, int NWG, int NPROD, int NST = 2>
@@ -876,6 +1033,77 @@ tgs_status launch_raster_tc_typed(const tgs_projected& p, const tgs_bins& b, int
   // 4x4 BF16: two producers (four slots), so that the doubled coefficient tiles fit in shared memory
   if (gw == 4 && gh == 4)
     return launch_cfg<BF, 4, 4, 4, BF ? 2 : 3>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
+  set_error("tensor-core path supports groups 1x1, 2x2, 4x2, 2x4, 4x4 (got %dx%d)", gw, gh);
+  return TGS_ERR_INVALID_ARGUMENT;
+}
+
+template <bool BF, int GW, int GH, int NWG, int NPROD, int NST = 2>
+tgs_status launch_batch_cfg(const RasterFrame* frames, int count, const tgs_raster_opts& o,
+                            int* next_item, uint64_t wait_ns, cudaStream_t st) {
+  using Cf = Cfg<GW, GH, NWG, NPROD, NST>;
+  using Sm = Smem<GW * GH, Cf::kSlots, BF ? 2 : 1>;
+  BatchArgs B{};
+  B.count = count;
+  int64_t total = 0;
+  for (int f = 0; f < count; ++f) {
+    const RasterFrame& r = frames[f];
+    const int TX = div_up(r.width, kTile), TY = div_up(r.height, kTile);
+    const int GX = div_up(TX, GW), GY = div_up(TY, GH);
+    if (((uintptr_t)r.p->mean2d & 7) || ((uintptr_t)r.p->conic_opacity & 15))
+      return set_error("frame %d: mean2d needs 8-byte and conic_opacity 16-byte alignment", f),
+             TGS_ERR_INVALID_ARGUMENT;
+    BatchFrame& d = B.f[f];
+    d.ranges = r.b->ranges;
+    d.vals = r.b->vals;
+    d.masks = r.b->masks;
+    d.mean2d = reinterpret_cast<const float2*>(r.p->mean2d);
+    d.conic_opacity = reinterpret_cast<const float4*>(r.p->conic_opacity);
+    d.rgb = r.p->rgb;
+    d.out_rgb = r.out_rgb;
+    d.out_T = r.out_T;
+    d.ready = r.ready;
+    d.status = r.status;
+    d.ready_value = r.ready_value;
+    d.width = r.width;
+    d.height = r.height;
+    d.GX = GX;
+    B.start[f] = (int32_t)total;
+    total += (int64_t)GX * GY;
+  }
+  if (total >= (int64_t(1) << 31)) return set_error("batch has too many tile groups"), TGS_ERR_INVALID_ARGUMENT;
+  B.start[count] = (int32_t)total;
+  int dev = 0, smem_sm = 0, sms = 0;
+  TGS_CUDA(cudaGetDevice(&dev));
+  TGS_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  TGS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // residency as in the single-frame launch: co-resident CTAs never wait for tensor memory
+  const int max_ctas = 512 / Cf::kTmemCols;
+  size_t smem = sizeof(Sm) + 1024 + 64;
+  smem = std::max(smem, (size_t)smem_sm / (max_ctas + 1) - 1024 + 16);
+  auto* k = k_raster_tc_batch<GW, GH, NWG, NPROD, NST, BF>;
+  TGS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  TGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, Cf::kThreads, smem));
+  const int grid = (int)std::min<int64_t>(std::max<int64_t>(total, 1), (int64_t)std::max(occ, 1) * sms);
+  TGS_CUDA(cudaMemsetAsync(next_item, 0, sizeof(int), st));
+  const float3 bg = make_float3(o.bg[0], o.bg[1], o.bg[2]);
+  const int cull = (o.flags & TGS_RASTER_NO_CULL) ? 0 : 1;
+  k<<<grid, Cf::kThreads, smem, st>>>(B, next_item, bg, device_error_word(), cull, wait_ns);
+  TGS_CHECK_LAUNCH("k_raster_tc_batch");
+  return TGS_OK;
+}
+
+template <bool BF>
+tgs_status launch_raster_tc_batch_typed(const RasterFrame* frames, int count, int gw, int gh,
+                                        const tgs_raster_opts& o, int* next_item, uint64_t wait_ns,
+                                        cudaStream_t st) {
+  constexpr int NST = BF ? 2 : 1;  // the configurations of the single-frame launch
+  if (gw == 1 && gh == 1) return launch_batch_cfg<BF, 1, 1, 1, 2>(frames, count, o, next_item, wait_ns, st);
+  if (gw == 2 && gh == 2) return launch_batch_cfg<BF, 2, 2, 4, 3, NST>(frames, count, o, next_item, wait_ns, st);
+  if (gw == 4 && gh == 2) return launch_batch_cfg<BF, 4, 2, 4, 3, NST>(frames, count, o, next_item, wait_ns, st);
+  if (gw == 2 && gh == 4) return launch_batch_cfg<BF, 2, 4, 4, 3, NST>(frames, count, o, next_item, wait_ns, st);
+  if (gw == 4 && gh == 4)
+    return launch_batch_cfg<BF, 4, 4, 4, BF ? 2 : 3>(frames, count, o, next_item, wait_ns, st);
   set_error("tensor-core path supports groups 1x1, 2x2, 4x2, 2x4, 4x4 (got %dx%d)", gw, gh);
   return TGS_ERR_INVALID_ARGUMENT;
 }

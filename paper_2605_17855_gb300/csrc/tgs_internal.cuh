@@ -57,6 +57,23 @@ tgs_status launch_raster_tc(const tgs_projected& p, const tgs_bins& b, int width
 tgs_status launch_raster_tc_bf16(const tgs_projected& p, const tgs_bins& b, int width, int height, int gw,
                             int gh, const tgs_raster_opts& o, float* out_rgb, float* out_T,
                             int32_t* n_contrib, cudaStream_t st);
+// One frame of a batched tensor-core rasterization (tgs_rasterize_batch).
+struct RasterFrame {
+  const tgs_projected* p;
+  const tgs_bins* b;
+  int width, height;
+  float* out_rgb;
+  float* out_T;
+  const int32_t* ready;
+  int32_t ready_value;
+  int32_t* status;
+};
+tgs_status launch_raster_tc_batch(const RasterFrame* frames, int count, int gw, int gh,
+                                  const tgs_raster_opts& o, int* next_item, uint64_t wait_ns,
+                                  cudaStream_t st);
+tgs_status launch_raster_tc_batch_bf16(const RasterFrame* frames, int count, int gw, int gh,
+                                       const tgs_raster_opts& o, int* next_item, uint64_t wait_ns,
+                                       cudaStream_t st);
 tgs_status launch_raster_backward(const tgs_projected& p, int64_t n, const tgs_bins& b, int width,
                                   int height, int gw, int gh, const tgs_raster_opts& o,
                                   const float* out_T, const int32_t* n_contrib, const float* grad_rgb,
@@ -161,6 +178,10 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
       : "r"(smem_addr(bar)), "r"(parity)
       : "memory");
   return ok != 0;
+}
+// Invalidates an mbarrier (no operation may be pending on it), so its memory can be re-initialized.
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 // Arrive `count` times at once.
 __device__ __forceinline__ void mbar_arrive_n(uint64_t* bar, uint32_t count) {

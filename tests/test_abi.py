@@ -100,7 +100,7 @@ def _imports(path):
 def test_product_never_imports_the_oracle():
     for p in glob.glob(os.path.join(ROOT, "paper_2605_17855_gb300", "**", "*.py"), recursive=True):
         assert "oracle" not in _imports(p), p
-    for p in glob.glob(os.path.join(ROOT, "paper_2605_17855_gb300", "csrc", "*")):
+    for p in glob.glob(os.path.join(ROOT, "paper_2605_17855_gb300", "csrc", "**", "*.*"), recursive=True):
         assert "oracle" not in open(p).read().lower(), p
 
 
@@ -167,7 +167,7 @@ def test_every_allocation_goes_through_the_counted_helpers():
     # tgs_allocation_count is only meaningful if no source allocates around it
     pat = re.compile(r"\bcuda(Malloc|MallocHost|MallocManaged|MallocAsync|HostAlloc|MallocPitch|"
                      r"Malloc3D|MallocArray)\s*\(")
-    for p in glob.glob(os.path.join(ROOT, "paper_2605_17855_gb300", "csrc", "*")):
+    for p in glob.glob(os.path.join(ROOT, "paper_2605_17855_gb300", "csrc", "**", "*.*"), recursive=True):
         src = re.sub(r"//[^\n]*", "", re.sub(r"/\*.*?\*/", "", open(p).read(), flags=re.S))
         src = re.sub(r'"(?:[^"\\\n]|\\.)*"', '""', src)  # string literals (error messages)
         hits = pat.findall(src)
