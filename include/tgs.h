@@ -220,8 +220,11 @@ tgs_status tgs_rasterize(const tgs_projected* proj, int64_t n, const tgs_bins* b
  * If frames[f].ready != NULL, frame f's items start only once *ready >= ready_value (device int32,
  * e.g. set by the stream that bins the frame): each CTA waits for it at most wait_limit_ns
  * (<= 0: 2 s); on expiry *status (if non-NULL) is set to TGS_ERR_TIMEOUT and the frame's items
- * are skipped, their pixels left unwritten. status (device int32, optional) is written only on
- * failure: the caller sets it to TGS_OK before the call. Precision FP16_TC or BF16_TC (FP32:
+ * are skipped, their pixels left unwritten. status (int32 in device or host-mapped memory,
+ * optional) is written only on failure: the caller sets it to TGS_OK before the call. done (int32
+ * in device or host-mapped memory, optional) is set to done_value once every item of the frame has
+ * been rendered or skipped (after a system-scope fence): a host thread polling it knows when the
+ * frame's pixels and status are final, before the whole launch ends. Precision FP16_TC or BF16_TC (FP32:
  * TGS_ERR_INVALID_ARGUMENT; use tgs_rasterize); opts->counters must be NULL. `workspace` is
  * TGS_BATCH_WORKSPACE_BYTES of device memory (the work counter; cleared by the call), owned by the
  * caller and not shared by overlapping calls. Errors: INVALID_ARGUMENT for count outside
@@ -237,7 +240,9 @@ typedef struct {
   float* out_T;              /* device [H,W] */
   const int32_t* ready;      /* optional device readiness flag */
   int32_t ready_value;
-  int32_t* status;           /* optional device status word */
+  int32_t* status;           /* optional status word */
+  int32_t* done;             /* optional completion word */
+  int32_t done_value;
 } tgs_frame;
 
 tgs_status tgs_rasterize_batch(const tgs_frame* frames, int32_t count, const tgs_tiling* tiling,
@@ -273,13 +278,17 @@ tgs_status tgs_last_device_error(int32_t reset);
 /* ---------------------------------------------------------------------------------------------
  * Rendering service (tgs_serve_*): resident scenes and asynchronous frame requests.
  *
- * A server owns device copies of its scenes and a worker thread that renders requests with the
- * calls above (preprocess, bin sort, rasterize). It keeps `slots` frames in flight, each on its own
- * CUDA stream with its own buffers; a request enters a slot as soon as one frees (continuous
- * batching: requests of different scenes and resolutions overlap on the GPU), in submission
- * order. All device memory of the server (scenes and slot buffers) counts against
- * hbm_budget_bytes. A slot's bin capacity starts at 4 entries per Gaussian and grows when a frame
- * needs more (the frame is then rendered again; counted in `regrown`).
+ * A server owns device copies of its scenes, `slots` sets of frame buffers and a worker thread.
+ * Every buffer is allocated by tgs_serve_create (slots) and tgs_serve_add_scene (scenes), charged
+ * to hbm_budget_bytes; the worker allocates nothing. A request enters a free slot in submission
+ * order and is preprocessed and binned there (the calls above, on the slot's own stream), so
+ * requests of different scenes and resolutions overlap on the GPU. With a tensor-core precision
+ * the worker then rasterizes every binned request together in ONE persistent launch
+ * (tgs_rasterize_batch; at most two launches in flight), so requests that arrive while a launch
+ * runs are binned meanwhile and join the next one (continuous batching); with FP32 each slot
+ * rasterizes on its own stream. The batched launch waits (bounded, 2 s) on a per-slot device
+ * readiness flag; every slot has its own device status word, so a time-out in one frame is
+ * reported for that request only.
  *
  * Requests are identified by tickets. A ticket's record is released when poll or wait reports it
  * done; later calls with it return TGS_ERR_NOT_FOUND. Waits are bounded: tgs_serve_wait returns
@@ -290,12 +299,16 @@ tgs_status tgs_last_device_error(int32_t reset);
 typedef struct {
   int64_t hbm_budget_bytes;   /* device bytes the server may hold (scenes + slot buffers) */
   int32_t max_inflight;       /* queued + rendering requests admitted at once (>= 1) */
-  int32_t slots;              /* frames rendered concurrently (1..16) */
+  int32_t slots;              /* frames in flight (1..16), each with its own buffers */
   int32_t device;             /* CUDA device ordinal (must be sm_103) */
   int32_t precision;          /* TGS_PRECISION_* */
-  tgs_tiling tiling;          /* tile grouping of every frame */
+  tgs_tiling tiling;          /* tile grouping (and binning flags) of every frame */
   float bg[3];                /* background colour */
   int32_t request_timeout_ms; /* 0 = no limit */
+  int64_t max_gaussians;      /* largest scene a slot renders (1 .. 2^30 - 1) */
+  int32_t max_width, max_height; /* largest frame a slot renders (1 .. 16384 each) */
+  int64_t max_entries;        /* bin entries a frame may need (1 .. 2^30 - 1); a frame that needs
+                                 more completes with TGS_ERR_CAPACITY */
 } tgs_serve_config;
 
 typedef struct tgs_server tgs_server; /* opaque */
@@ -312,7 +325,7 @@ typedef struct {
   int64_t rejected;           /* submissions refused with TGS_ERR_BUSY */
   int64_t completed;          /* requests completed with TGS_OK */
   int64_t failed;             /* requests completed with an error (including time-outs) */
-  int64_t regrown;            /* frames rendered again after a bin capacity increase */
+  int64_t regrown;            /* unused (0): slot capacities are fixed at creation */
   int64_t inflight;           /* queued + rendering now */
   int64_t hbm_bytes;          /* device bytes held by the server now */
   double seconds;             /* since tgs_serve_create */
@@ -321,12 +334,14 @@ typedef struct {
   tgs_serve_resolution_stats res[TGS_SERVE_MAX_RESOLUTIONS]; /* in order of first appearance */
 } tgs_serve_stats;
 
-/* Creates a server and its worker thread on config->device. INVALID_ARGUMENT for a bad config,
- * UNSUPPORTED_DEVICE if the device is not sm_103, CUDA if a stream cannot be created. */
+/* Creates a server, its slot buffers (sized by the max_* fields) and its worker thread on
+ * config->device. INVALID_ARGUMENT for a bad config, CAPACITY if the slot buffers exceed the
+ * budget, UNSUPPORTED_DEVICE if the device is not sm_103, CUDA if an allocation or a stream fails. */
 tgs_status tgs_serve_create(const tgs_serve_config* config, tgs_server** out);
 
 /* Copies a scene (the arrays of `scene` may be host or device memory) into server-owned device
- * memory and returns its id. CAPACITY if the copy would exceed the budget. Synchronous. */
+ * memory and returns its id. CAPACITY if the copy would exceed the budget or the scene has more
+ * than max_gaussians Gaussians. Synchronous. */
 tgs_status tgs_serve_add_scene(tgs_server* server, const tgs_scene* scene, int32_t* scene_id);
 
 /* Frees a scene. BUSY while admitted requests use it, NOT_FOUND for an unknown id. */
@@ -336,7 +351,8 @@ tgs_status tgs_serve_remove_scene(tgs_server* server, int32_t scene_id);
  * if non-NULL, out_T (device [H,W]); both are caller-owned and must stay valid until the request
  * is done. Returns at once with a ticket. BUSY if max_inflight requests are admitted already;
  * NOT_FOUND for an unknown scene; INVALID_ARGUMENT for a bad camera or NULL out_rgb. A request
- * whose buffers cannot fit the budget completes with CAPACITY. */
+ * larger than max_width x max_height, or whose frame needs more than max_entries bin entries,
+ * completes with CAPACITY. */
 tgs_status tgs_serve_submit(tgs_server* server, int32_t scene_id, const tgs_camera* camera,
                             float* out_rgb, float* out_T, uint64_t* ticket);
 

@@ -84,7 +84,8 @@ RASTER_NO_CULL = 1
 class _Frame(C.Structure):
     _fields_ = [("proj", C.POINTER(_Projected)), ("n", C.c_int64), ("bins", C.POINTER(_Bins)),
                 ("width", C.c_int32), ("height", C.c_int32), ("out_rgb", C.c_void_p), ("out_T", C.c_void_p),
-                ("ready", C.c_void_p), ("ready_value", C.c_int32), ("status", C.c_void_p)]
+                ("ready", C.c_void_p), ("ready_value", C.c_int32), ("status", C.c_void_p),
+                ("done", C.c_void_p), ("done_value", C.c_int32)]
 
 
 BATCH_MAX_FRAMES = 32
@@ -99,7 +100,8 @@ _lock = threading.Lock()
 class _ServeConfig(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_inflight", C.c_int32), ("slots", C.c_int32),
                 ("device", C.c_int32), ("precision", C.c_int32), ("tiling", _Tiling),
-                ("bg", C.c_float * 3), ("request_timeout_ms", C.c_int32)]
+                ("bg", C.c_float * 3), ("request_timeout_ms", C.c_int32), ("max_gaussians", C.c_int64),
+                ("max_width", C.c_int32), ("max_height", C.c_int32), ("max_entries", C.c_int64)]
 
 
 SERVE_MAX_RESOLUTIONS = 16
@@ -405,6 +407,8 @@ class BatchFrame:
     ready: "object" = None
     ready_value: int = 1
     status: "object" = None
+    done: "object" = None
+    done_value: int = 1
 
 
 def rasterize_batch(frames, tiling=(2, 2), precision="fp16_tc", bg=(0.0, 0.0, 0.0), wait_limit_ns=0,
@@ -423,7 +427,8 @@ def rasterize_batch(frames, tiling=(2, 2), precision="fp16_tc", bg=(0.0, 0.0, 0.
         ps, bs = f.proj.struct(), f.bins.struct()
         keep += [ps, bs]
         arr[k] = _Frame(C.pointer(ps), f.proj.n, C.pointer(bs), int(f.width), int(f.height), _ptr(f.out_rgb),
-                        _ptr(f.out_T), _ptr(f.ready), int(f.ready_value), _ptr(f.status))
+                        _ptr(f.out_T), _ptr(f.ready), int(f.ready_value), _ptr(f.status), _ptr(f.done),
+                        int(f.done_value))
     o = _RasterOpts(PRECISION[precision], 0 if cull else RASTER_NO_CULL,
                     (C.c_float * 3)(*[float(v) for v in bg]), None)
     t = _tiling(tiling)
@@ -642,11 +647,16 @@ class Server:
     or call close()."""
 
     def __init__(self, hbm_budget_bytes: int, max_inflight: int = 64, slots: int = 4, device: int = 0,
-                 precision: str = "fp16_tc", tiling=(2, 2), bg=(0.0, 0.0, 0.0), request_timeout_ms: int = 0):
+                 precision: str = "fp16_tc", tiling=(2, 2), bg=(0.0, 0.0, 0.0), request_timeout_ms: int = 0,
+                 max_gaussians: int = 1 << 18, max_size=(1024, 1024), max_entries: int = 1 << 22,
+                 membership: bool = True):
+        """Slot capacities (max_gaussians, max_size = (width, height), max_entries) are fixed here:
+        the server allocates every slot buffer now, charged to the budget."""
         lib = load()
         cfg = _ServeConfig(int(hbm_budget_bytes), int(max_inflight), int(slots), int(device),
-                           PRECISION[precision], _tiling(tiling), (C.c_float * 3)(*[float(v) for v in bg]),
-                           int(request_timeout_ms))
+                           PRECISION[precision], _tiling(tiling, membership),
+                           (C.c_float * 3)(*[float(v) for v in bg]), int(request_timeout_ms),
+                           int(max_gaussians), int(max_size[0]), int(max_size[1]), int(max_entries))
         h = _P()
         _check(lib.tgs_serve_create(C.byref(cfg), C.byref(h)))
         self._h = h

@@ -246,7 +246,7 @@ tgs_status tgs_rasterize_batch(const tgs_frame* frames, int32_t count, const tgs
     }
     if (!fr.out_rgb || !fr.out_T) return set_error("frame %d: null output", f), TGS_ERR_INVALID_ARGUMENT;
     rf[f] = RasterFrame{fr.proj, fr.bins, fr.width, fr.height, fr.out_rgb, fr.out_T, fr.ready,
-                        fr.ready_value, fr.status};
+                        fr.ready_value, fr.status, fr.done, fr.done_value};
   }
   tgs_status s = require_current_sm103();
   if (s != TGS_OK) return s;

@@ -841,7 +841,7 @@ size_t bin_sort_workspace_bytes(int64_t n, int64_t capacity, int GX, int GY) {
 
 tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int height, int gw, int gh,
                            bool membership, void* ws, size_t ws_bytes, const tgs_bins& b,
-                           cudaStream_t st) {
+                           cudaStream_t st, int32_t* err_word) {
   (void)ws_bytes;
   const int n = (int)n64;
   const int TX = div_up(width, kTile), TY = div_up(height, kTile);
@@ -880,7 +880,7 @@ tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int h
   const int4* rect = reinterpret_cast<const int4*>(p.rect);
   const float2* m2 = reinterpret_cast<const float2*>(p.mean2d);
   const float4* co = reinterpret_cast<const float4*>(p.conic_opacity);
-  int32_t* err = device_error_word();
+  int32_t* err = err_word ? err_word : device_error_word();
   TGS_CUDA(cudaMemsetAsync(w + L.zero_begin, 0, L.zero_end - L.zero_begin, st));
 
   // 1. depth order of the visible Gaussians: compacted keys + digit histograms, then four

@@ -158,9 +158,11 @@ __device__ __forceinline__ float bf16_round(float x) {
   return __bfloat162float(__float2bfloat16_rn(x));
 }
 
+// The error word may be host-mapped memory (a batched frame's status word), so it is set with a
+// plain store: every writer stores the same value.
 __device__ __forceinline__ void record_abort(int* abort_flag, int32_t* err) {
   *reinterpret_cast<volatile int*>(abort_flag) = 1;
-  if (err) atomicExch(err, TGS_ERR_TIMEOUT);
+  if (err) *reinterpret_cast<volatile int32_t*>(err) = TGS_ERR_TIMEOUT;
 }
 
 // Blend state of one pixel. `thr` is log2(1/255) while the pixel is live and +inf once it has
@@ -862,10 +864,14 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
 // The work items are the (frame, tile group) pairs of all frames, numbered frame by frame. Each
 // CTA takes the next item from a device counter until none is left, so frames of any size and
 // resolution share the GPU in one launch; between items the CTA drains its tensor-core work and
-// re-initializes its barriers. Before the first item of a frame is rendered, the frame's readiness
-// flag (if any) must have reached its value: the CTA waits for it at most `wait_ns`; on expiry the
-// frame's status word becomes TGS_ERR_TIMEOUT and its items are skipped (their pixels are not
-// written), and items of a frame already marked failed are skipped at once.
+// re-initializes its barriers. A bounded wait that expires inside an item is reported to the
+// frame's status word (the launch's error word if it has none), and that CTA stops. Before an item
+// of a frame is rendered, the frame's readiness flag (if any) must have reached its value: the CTA
+// waits for it at most `wait_ns`; on expiry the frame's status word becomes TGS_ERR_TIMEOUT and its
+// items are skipped (their pixels are not written), and items of a frame already marked failed are
+// skipped at once. Once every item of a frame has been rendered or skipped, the CTA that finished
+// its last item sets the frame's done word (if any) to its value, after a system-scope fence, so
+// that a host thread polling it sees the frame's pixels and status final.
 constexpr int kMaxBatchFrames = 32;
 
 struct BatchFrame {
@@ -878,8 +884,9 @@ struct BatchFrame {
   float* out_rgb;
   float* out_T;
   const int32_t* ready;  // may be NULL
-  int32_t* status;       // may be NULL
-  int32_t ready_value;
+  int32_t* status;       // may be NULL (device or host-mapped memory)
+  int32_t* done;         // may be NULL (device or host-mapped memory)
+  int32_t ready_value, done_value;
   int32_t width, height, GX;
 };
 
@@ -905,6 +912,7 @@ template <int GW, int GH, int NWG, int NPROD, int NST, bool BF>
 __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NST)
     k_raster_tc_batch(const __grid_constant__ BatchArgs B, int* __restrict__ next_item, float3 bg,
                       int32_t* __restrict__ err, int cull, uint64_t wait_ns) {
+  // next_item[0]: the work counter; next_item[1 + f]: items of frame f finished
   using C = Cfg<GW, GH, NWG, NPROD, NST>;
   constexpr int TILES = C::kTiles;
   constexpr int SLOTS = C::kSlots;
@@ -936,7 +944,7 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
           run = 0;  // the frame has already failed
         } else if (fr.ready && !wait_flag(fr.ready, fr.ready_value, wait_ns)) {
           run = 0;
-          if (fr.status) atomicExch(fr.status, TGS_ERR_TIMEOUT);
+          if (fr.status) *reinterpret_cast<volatile int32_t*>(fr.status) = TGS_ERR_TIMEOUT;
         }
       }
       s_item = item;
@@ -951,12 +959,22 @@ __global__ void __launch_bounds__(Cfg<GW, GH, NWG, NPROD, NST>::kThreads, 2 / NS
       raster_group<GW, GH, NWG, NPROD, NST, BF, false, false>(
           S, S.tmem_base, item - B.start[f], fr.ranges, fr.vals, fr.masks, fr.mean2d,
           fr.conic_opacity, fr.rgb, fr.width, fr.height, fr.GX, bg, fr.out_rgb, fr.out_T, nullptr,
-          nullptr, err, cull);
+          nullptr, fr.status ? fr.status : err, cull);
     }
-    // every warp is done with the item and the MMA thread has drained its tensor-core work
+    // every warp is done with the item and the MMA thread has drained its tensor-core work; the
+    // item's pixels are visible device-wide before it is counted as finished
+    __threadfence();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (threadIdx.x == 0) {
+      const BatchFrame& fr = B.f[f];
+      const int items = B.start[f + 1] - B.start[f];
+      if (fr.done && atomicAdd(next_item + 1 + f, 1) == items - 1) {
+        __threadfence_system();
+        *reinterpret_cast<volatile int32_t*>(fr.done) = fr.done_value;
+      }
+    }
     if (S.abort) break;  // a bounded wait expired: this CTA stops (uniform: read after the barrier)
     if (threadIdx.x == 0 && s_run) {
       inval_group_state(S);
@@ -1063,7 +1081,9 @@ tgs_status launch_batch_cfg(const RasterFrame* frames, int count, const tgs_rast
     d.out_T = r.out_T;
     d.ready = r.ready;
     d.status = r.status;
+    d.done = r.done;
     d.ready_value = r.ready_value;
+    d.done_value = r.done_value;
     d.width = r.width;
     d.height = r.height;
     d.GX = GX;
@@ -1085,7 +1105,7 @@ tgs_status launch_batch_cfg(const RasterFrame* frames, int count, const tgs_rast
   int occ = 0;
   TGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, Cf::kThreads, smem));
   const int grid = (int)std::min<int64_t>(std::max<int64_t>(total, 1), (int64_t)std::max(occ, 1) * sms);
-  TGS_CUDA(cudaMemsetAsync(next_item, 0, sizeof(int), st));
+  TGS_CUDA(cudaMemsetAsync(next_item, 0, sizeof(int) * (1 + kMaxBatchFrames), st));
   const float3 bg = make_float3(o.bg[0], o.bg[1], o.bg[2]);
   const int cull = (o.flags & TGS_RASTER_NO_CULL) ? 0 : 1;
   k<<<grid, Cf::kThreads, smem, st>>>(B, next_item, bg, device_error_word(), cull, wait_ns);

@@ -1,14 +1,21 @@
-// Rendering service (tgs_serve_*): resident scenes, a worker thread and `slots` concurrent frames.
+// Rendering service (tgs_serve_*): resident scenes, a worker thread, `slots` concurrent frames
+// and batched tensor-core rasterization.
 //
-// The worker thread owns the slots. Each slot has its own CUDA stream, completion event and
-// buffers (projected Gaussians, bins, bin-sort workspace, a T buffer when the caller passes none,
-// and a pinned host word pair for the entry count and the device error word). A request is moved
-// from the queue into a free slot and rendered there by the library's own calls (preprocess, bin
-// sort, rasterize), all asynchronous on the slot's stream; the worker polls the slots' events, so
-// frames of different requests, scenes and resolutions overlap on the GPU (continuous batching at
-// request granularity). A frame whose bins overflowed the slot's capacity is rendered again after
-// the capacity has grown. Scene memory and slot buffers are charged to the budget before they are
-// allocated.
+// Every device buffer is allocated on the client's thread: one block per slot at creation (sized
+// for max_gaussians, max_width x max_height and max_entries) and one block per scene; the worker
+// thread allocates nothing. Each slot has its own stream, its buffers (projected Gaussians, bins,
+// bin-sort workspace, a T image for requests that bring none) and three device words: a readiness
+// flag, a status word and the bin sort's error word.
+//
+// The worker moves queued requests into free slots and preprocesses and bins them there,
+// asynchronously on the slot's stream (frames of different scenes and resolutions overlap on the
+// GPU). With a tensor-core precision, the slots whose binning has finished are then rasterized
+// together by one persistent launch (tgs_rasterize_batch over (frame, tile group) work items) on
+// the batch stream; up to two launches are in flight, and requests that arrive meanwhile are binned
+// and join the next launch (continuous batching). The launch waits (bounded) on each slot's
+// readiness flag, which the slot's stream raises after binning, and reports a time-out to that
+// slot's status word only. With FP32 each slot rasterizes on its own stream.
+#include <algorithm>
 #include <atomic>
 #include <thread>
 #include <unordered_map>
@@ -24,9 +31,9 @@ using serve::Core;
 using serve::Request;
 
 constexpr int kMaxSlots = 16;
-constexpr double kInitialEntriesPerGaussian = 4.0;
-constexpr double kGrowth = 1.25;
-constexpr int kDrainLimitMs = 10000;  // destroy: longest wait for frames still on the GPU
+constexpr int kMaxBatches = 2;              // batched launches in flight
+constexpr int kDrainLimitMs = 10000;        // destroy: longest wait for frames still on the GPU
+constexpr uint64_t kReadyWaitNs = 2000000000ull;
 
 struct SceneRec {
   tgs_scene s{};  // device pointers into `mem`
@@ -34,45 +41,48 @@ struct SceneRec {
   size_t bytes = 0;
 };
 
+// Pinned host words of a slot. num_entries and sort_error are copied back after binning; status
+// and done are written by the batched launch itself (pinned memory is mapped into the device's
+// address space), so the worker sees a frame finish as soon as its last tile group is rendered.
 struct Readback {
   int64_t num_entries;
-  int32_t device_error;
+  int32_t sort_error;  // the bin sort's error word
+  int32_t status;      // the frame's status word in the batched launch
+  int32_t done;        // set to the slot's sequence number when the frame is complete
   int32_t pad;
 };
 
+enum class SlotState { kFree, kBinning, kReady, kRaster };
+
 struct Slot {
   cudaStream_t stream = nullptr;
-  cudaEvent_t done = nullptr;
-  Readback* host = nullptr;  // pinned
-  // buffers and their sizes
-  void* proj_mem = nullptr;
-  int64_t proj_n = 0;
+  cudaEvent_t done = nullptr;  // binning done (tensor cores) or frame done (FP32)
+  Readback* host = nullptr;    // pinned
+  void* mem = nullptr;         // every device buffer of the slot
   tgs_projected proj{};
-  void* bins_mem = nullptr;
-  int64_t bins_cap = 0;
-  int64_t bins_groups = 0;
   tgs_bins bins{};
   void* ws = nullptr;
   size_t ws_bytes = 0;
   float* T = nullptr;
-  int64_t T_px = 0;
-  size_t bytes = 0;  // device bytes charged
-  // the request in flight
-  bool busy = false;
+  int32_t* words = nullptr;    // [0] readiness flag, [1] status, [2] bin-sort error word
+  int32_t seq = 0;             // value of the readiness flag for the request in the slot
+  SlotState state = SlotState::kFree;
+  int batch = -1;  // the batched launch rasterizing the slot's frame
   bool timed_out = false;
   Request req{};
   int64_t scene_n = 0;
 };
 
+struct Batch {
+  cudaEvent_t done = nullptr;
+  int* counter = nullptr;  // device work counter (tgs_rasterize_batch workspace)
+  std::vector<int> slots;
+  bool busy = false;
+};
+
 inline size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
-size_t projected_bytes(int64_t n) {
-  return a256(8 * n) + a256(16 * n) + a256(12 * n) + a256(4 * n) + a256(4 * n) + a256(16 * n);
-}
-
-size_t bins_bytes(int64_t cap, int64_t groups) {
-  return a256(4 * cap) + a256(2 * cap) + a256(8 * groups) + a256(8);
-}
+__global__ void k_set_flag(int32_t* flag, int32_t value) { *flag = value; }
 
 }  // namespace
 }  // namespace tgs
@@ -85,12 +95,16 @@ struct tgs_server {
   std::unordered_map<int32_t, tgs::SceneRec> scenes;
   int32_t next_scene = 0;
   std::atomic<int64_t> hbm{0};
-  std::atomic<int64_t> regrown{0};
   std::vector<tgs::Slot> slots;
+  tgs::Batch batches[tgs::kMaxBatches];
+  cudaStream_t batch_stream = nullptr;
+  void* batch_mem = nullptr;
+  size_t slot_bytes = 0;
   std::atomic<bool> drained{true};
-  int32_t* err_word = nullptr;
 
   explicit tgs_server(const tgs_serve_config& c) : cfg(c), core(c.max_inflight, c.request_timeout_ms) {}
+
+  bool tensor_cores() const { return cfg.precision != TGS_PRECISION_FP32; }
 
   // Charges `bytes` to the budget; false if they do not fit.
   bool reserve(size_t bytes) {
@@ -106,112 +120,60 @@ struct tgs_server {
 namespace tgs {
 namespace {
 
-void free_slot_buffers(tgs_server* S, Slot& sl) {
-  cudaFree(sl.proj_mem);
-  cudaFree(sl.bins_mem);
-  cudaFree(sl.ws);
-  cudaFree(sl.T);
-  sl.proj_mem = sl.bins_mem = sl.ws = nullptr;
-  sl.T = nullptr;
-  sl.proj_n = sl.bins_cap = sl.bins_groups = sl.T_px = 0;
-  sl.ws_bytes = 0;
-  S->unreserve(sl.bytes);
-  sl.bytes = 0;
+int64_t max_groups(const tgs_serve_config& c) {
+  return (int64_t)div_up(div_up(c.max_width, kTile), c.tiling.group_w) *
+         div_up(div_up(c.max_height, kTile), c.tiling.group_h);
 }
 
-// Makes the slot's buffers large enough for n Gaussians, `cap` bin entries, the image and (if the
-// caller gave no T buffer) a T image. Buffers only grow; a grown buffer is reallocated (the slot
-// is idle). Returns TGS_ERR_CAPACITY if the budget cannot hold them.
-tgs_status ensure_buffers(tgs_server* S, Slot& sl, int64_t n, int64_t cap, const tgs_camera& cam,
-                          bool need_T) {
-  const int TX = div_up(cam.width, kTile), TY = div_up(cam.height, kTile);
-  const int64_t groups =
-      (int64_t)div_up(TX, S->cfg.tiling.group_w) * div_up(TY, S->cfg.tiling.group_h);
-  size_t ws_need = 0;
-  tgs_status s = tgs_bin_sort_workspace_size(n, cap, cam.width, cam.height, &S->cfg.tiling, &ws_need);
-  if (s != TGS_OK) return s;
-  const int64_t px = need_T ? (int64_t)cam.width * cam.height : 0;
-  // Replaces *mem (old_bytes) by a buffer of new_bytes. The new size is charged first; if it does
-  // not fit, nothing changes. *lost tells whether the old buffer is gone (a failed allocation).
-  bool lost = false;
-  auto grow = [&](void** mem, size_t old_bytes, size_t new_bytes) -> tgs_status {
-    lost = false;
-    if (!S->reserve(new_bytes)) {
-      set_error("serving budget of %lld bytes exceeded", (long long)S->cfg.hbm_budget_bytes);
-      return TGS_ERR_CAPACITY;
-    }
-    cudaFree(*mem);
-    *mem = nullptr;
-    lost = true;
-    S->unreserve(old_bytes);
-    sl.bytes -= old_bytes;
-    const cudaError_t e = device_malloc(mem, new_bytes);
-    if (e != cudaSuccess) {
-      S->unreserve(new_bytes);
-      return cuda_status(e, "cudaMalloc (serving slot)");
-    }
-    sl.bytes += new_bytes;
-    return TGS_OK;
+// Bytes of one slot's buffers, and their layout inside the slot's block when `sl` is given.
+size_t slot_layout(const tgs_serve_config& c, Slot* sl) {
+  const int64_t n = c.max_gaussians, cap = c.max_entries, G = max_groups(c);
+  const int GX = div_up(div_up(c.max_width, kTile), c.tiling.group_w);
+  const int GY = div_up(div_up(c.max_height, kTile), c.tiling.group_h);
+  const size_t ws = bin_sort_workspace_bytes(n, cap, GX, GY);
+  char* p = sl ? static_cast<char*>(sl->mem) : nullptr;
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    char* q = p ? p + off : nullptr;
+    off += a256(b);
+    return q;
   };
-  if (n > sl.proj_n) {
-    s = grow(&sl.proj_mem, sl.proj_n ? projected_bytes(sl.proj_n) : 0, projected_bytes(n));
-    if (s != TGS_OK) {
-      if (lost) sl.proj_n = 0;
-      return s;
-    }
-    sl.proj_n = n;
-    char* p = static_cast<char*>(sl.proj_mem);
-    size_t off = 0;
-    auto take = [&](size_t b) { char* q = p + off; off += a256(b); return q; };
-    sl.proj.mean2d = reinterpret_cast<float*>(take(8 * n));
-    sl.proj.conic_opacity = reinterpret_cast<float*>(take(16 * n));
-    sl.proj.rgb = reinterpret_cast<float*>(take(12 * n));
-    sl.proj.depth = reinterpret_cast<float*>(take(4 * n));
-    sl.proj.radius = reinterpret_cast<int32_t*>(take(4 * n));
-    sl.proj.rect = reinterpret_cast<int32_t*>(take(16 * n));
+  char* mean2d = take(8 * n);
+  char* conic = take(16 * n);
+  char* rgb = take(12 * n);
+  char* depth = take(4 * n);
+  char* radius = take(4 * n);
+  char* rect = take(16 * n);
+  char* vals = take(4 * cap);
+  char* masks = take(2 * cap);
+  char* ranges = take(8 * G);
+  char* count = take(8);
+  char* wsp = take(ws);
+  char* T = take(4 * (size_t)c.max_width * c.max_height);
+  char* words = take(16);
+  if (sl) {
+    sl->proj.mean2d = reinterpret_cast<float*>(mean2d);
+    sl->proj.conic_opacity = reinterpret_cast<float*>(conic);
+    sl->proj.rgb = reinterpret_cast<float*>(rgb);
+    sl->proj.depth = reinterpret_cast<float*>(depth);
+    sl->proj.radius = reinterpret_cast<int32_t*>(radius);
+    sl->proj.rect = reinterpret_cast<int32_t*>(rect);
+    sl->bins.capacity = cap;
+    sl->bins.keys = nullptr;
+    sl->bins.vals = reinterpret_cast<uint32_t*>(vals);
+    sl->bins.masks = reinterpret_cast<uint16_t*>(masks);
+    sl->bins.ranges = reinterpret_cast<uint32_t*>(ranges);
+    sl->bins.num_entries = reinterpret_cast<int64_t*>(count);
+    sl->ws = wsp;
+    sl->ws_bytes = ws;
+    sl->T = reinterpret_cast<float*>(T);
+    sl->words = reinterpret_cast<int32_t*>(words);
   }
-  if (cap > sl.bins_cap || groups > sl.bins_groups) {
-    const int64_t nc = std::max(cap, sl.bins_cap), ng = std::max(groups, sl.bins_groups);
-    s = grow(&sl.bins_mem, sl.bins_cap ? bins_bytes(sl.bins_cap, sl.bins_groups) : 0,
-             bins_bytes(nc, ng));
-    if (s != TGS_OK) {
-      if (lost) sl.bins_cap = sl.bins_groups = 0;
-      return s;
-    }
-    sl.bins_cap = nc;
-    sl.bins_groups = ng;
-    char* p = static_cast<char*>(sl.bins_mem);
-    size_t off = 0;
-    auto take = [&](size_t b) { char* q = p + off; off += a256(b); return q; };
-    sl.bins.capacity = nc;
-    sl.bins.keys = nullptr;
-    sl.bins.vals = reinterpret_cast<uint32_t*>(take(4 * nc));
-    sl.bins.masks = reinterpret_cast<uint16_t*>(take(2 * nc));
-    sl.bins.ranges = reinterpret_cast<uint32_t*>(take(8 * ng));
-    sl.bins.num_entries = reinterpret_cast<int64_t*>(take(8));
-  }
-  if (ws_need > sl.ws_bytes) {
-    s = grow(&sl.ws, sl.ws_bytes, ws_need);
-    if (s != TGS_OK) {
-      if (lost) sl.ws_bytes = 0;
-      return s;
-    }
-    sl.ws_bytes = ws_need;
-  }
-  if (px > sl.T_px) {
-    void* m = sl.T;
-    s = grow(&m, 4 * (size_t)sl.T_px, 4 * (size_t)px);
-    sl.T = static_cast<float*>(m);
-    if (s != TGS_OK) {
-      if (lost) sl.T_px = 0;
-      return s;
-    }
-    sl.T_px = px;
-  }
-  return TGS_OK;
+  return off;
 }
 
-// Enqueues the frame of the slot's request on its stream. On failure the caller completes it.
+// Enqueues preprocess + bin sort of the slot's request on its stream (and, with FP32, the
+// rasterization). On failure the caller completes the request.
 tgs_status issue(tgs_server* S, Slot& sl) {
   const Request& r = sl.req;
   tgs_scene scene;
@@ -221,32 +183,40 @@ tgs_status issue(tgs_server* S, Slot& sl) {
     if (it == S->scenes.end()) return set_error("scene %d was removed", r.scene), TGS_ERR_NOT_FOUND;
     scene = it->second.s;  // kept alive by the request's scene reference
   }
+  if (r.camera.width > S->cfg.max_width || r.camera.height > S->cfg.max_height)
+    return set_error("a %dx%d frame exceeds the slots' %dx%d", r.camera.width, r.camera.height,
+                     S->cfg.max_width, S->cfg.max_height),
+           TGS_ERR_CAPACITY;
   sl.scene_n = scene.n;
-  const int64_t want = std::max<int64_t>(
-      sl.bins_cap, (int64_t)(kInitialEntriesPerGaussian * (double)scene.n) + 4096);
-  tgs_status s = ensure_buffers(S, sl, std::max<int64_t>(scene.n, 1), want, r.camera, !r.out_T);
-  if (s != TGS_OK) return s;
   cudaStream_t st = sl.stream;
-  s = tgs_preprocess(&scene, &r.camera, &sl.proj, st);
+  ++sl.seq;
+  TGS_CUDA(cudaMemsetAsync(sl.words + 1, 0, 2 * sizeof(int32_t), st));  // status, error word
+  tgs_status s = TGS_OK;
+  if (scene.n > 0) {
+    s = launch_preprocess(scene, r.camera, sl.proj, st);
+    if (s != TGS_OK) return s;
+  }
+  s = launch_bin_sort(sl.proj, scene.n, r.camera.width, r.camera.height, S->cfg.tiling.group_w,
+                      S->cfg.tiling.group_h, (S->cfg.tiling.flags & TGS_BIN_RANGE_ONLY) == 0, sl.ws,
+                      sl.ws_bytes, sl.bins, st, sl.words + 2);
   if (s != TGS_OK) return s;
-  s = tgs_bin_sort(&sl.proj, scene.n, r.camera.width, r.camera.height, &S->cfg.tiling, sl.ws,
-                   sl.ws_bytes, &sl.bins, nullptr, st);
-  if (s != TGS_OK) return s;
-  tgs_raster_opts o{};
-  o.precision = S->cfg.precision;
-  o.flags = 0;
-  o.bg[0] = S->cfg.bg[0];
-  o.bg[1] = S->cfg.bg[1];
-  o.bg[2] = S->cfg.bg[2];
-  o.counters = nullptr;
-  s = tgs_rasterize(&sl.proj, scene.n, &sl.bins, r.camera.width, r.camera.height, &S->cfg.tiling, &o,
-                    r.out_rgb, r.out_T ? r.out_T : sl.T, nullptr, st);
-  if (s != TGS_OK) return s;
+  if (!S->tensor_cores()) {
+    tgs_raster_opts o{};
+    o.precision = TGS_PRECISION_FP32;
+    for (int k = 0; k < 3; ++k) o.bg[k] = S->cfg.bg[k];
+    s = launch_raster_fp32(sl.proj, sl.bins, r.camera.width, r.camera.height, S->cfg.tiling.group_w,
+                           S->cfg.tiling.group_h, o, r.out_rgb, r.out_T ? r.out_T : sl.T, nullptr, st);
+    if (s != TGS_OK) return s;
+  } else {
+    k_set_flag<<<1, 1, 0, st>>>(sl.words, sl.seq);
+    TGS_CHECK_LAUNCH("k_set_flag");
+  }
   TGS_CUDA(cudaMemcpyAsync(&sl.host->num_entries, sl.bins.num_entries, sizeof(int64_t),
                            cudaMemcpyDeviceToHost, st));
-  TGS_CUDA(cudaMemcpyAsync(&sl.host->device_error, S->err_word, sizeof(int32_t),
-                           cudaMemcpyDeviceToHost, st));
+  TGS_CUDA(cudaMemcpyAsync(&sl.host->sort_error, sl.words + 2, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           st));
   TGS_CUDA(cudaEventRecord(sl.done, st));
+  sl.state = SlotState::kBinning;
   return TGS_OK;
 }
 
@@ -255,32 +225,61 @@ tgs_status issue(tgs_server* S, Slot& sl) {
 void finish(tgs_server* S, Slot& sl, tgs_status st) {
   S->core.release(sl.req);
   S->core.complete(sl.req.ticket, st);
-  sl.busy = false;
+  sl.state = SlotState::kFree;
+  sl.batch = -1;
   sl.timed_out = false;
 }
 
-// Handles a slot whose event has completed.
-void on_done(tgs_server* S, Slot& sl) {
-  if (sl.host->device_error != TGS_OK) {
-    // a bounded device wait expired in this frame (the error word is shared by the device)
-    cudaMemsetAsync(S->err_word, 0, sizeof(int32_t), sl.stream);
-    finish(S, sl, TGS_ERR_TIMEOUT);
-    return;
+int32_t host_word(const int32_t* w) { return *reinterpret_cast<const volatile int32_t*>(w); }
+
+// Status of a frame whose binning (and, with FP32, rasterization) has completed.
+tgs_status binning_status(const tgs_server* S, const Slot& sl) {
+  if (sl.host->sort_error != TGS_OK) return TGS_ERR_TIMEOUT;
+  if (sl.host->num_entries > S->cfg.max_entries) return TGS_ERR_CAPACITY;
+  return TGS_OK;
+}
+
+// Rasterizes every binned slot with one persistent tensor-core launch on the batch stream, the
+// frames ordered from the fewest pixels to the most (small frames complete first).
+tgs_status launch_batch(tgs_server* S, int bi) {
+  Batch& b = S->batches[bi];
+  b.slots.clear();
+  for (int k = 0; k < (int)S->slots.size(); ++k)
+    if (S->slots[k].state == SlotState::kReady) b.slots.push_back(k);
+  if (b.slots.empty()) return TGS_OK;
+  auto pixels = [&](int k) {
+    const tgs_camera& c = S->slots[k].req.camera;
+    return (int64_t)c.width * c.height;
+  };
+  std::stable_sort(b.slots.begin(), b.slots.end(), [&](int x, int y) { return pixels(x) < pixels(y); });
+  RasterFrame rf[kMaxSlots];
+  int count = 0;
+  for (int k : b.slots) {
+    Slot& sl = S->slots[k];
+    TGS_CUDA(cudaStreamWaitEvent(S->batch_stream, sl.done, 0));
+    sl.host->status = TGS_OK;
+    sl.host->done = 0;
+    const Request& r = sl.req;
+    rf[count++] = RasterFrame{&sl.proj, &sl.bins, r.camera.width, r.camera.height, r.out_rgb,
+                              r.out_T ? r.out_T : sl.T, sl.words, sl.seq, &sl.host->status,
+                              &sl.host->done, sl.seq};
   }
-  const int64_t need = sl.host->num_entries;
-  if (need > sl.bins_cap && !sl.timed_out) {  // overflow: grow and render again
-    const int64_t cap = (int64_t)(kGrowth * (double)need) + 4096;
-    tgs_status s = ensure_buffers(S, sl, std::max<int64_t>(sl.scene_n, 1), cap, sl.req.camera,
-                                  !sl.req.out_T);
-    if (s == TGS_OK) s = issue(S, sl);
-    if (s != TGS_OK) {
-      finish(S, sl, s);
-      return;
-    }
-    S->regrown.fetch_add(1);
-    return;  // still busy
+  tgs_raster_opts o{};
+  o.precision = S->cfg.precision;
+  for (int k = 0; k < 3; ++k) o.bg[k] = S->cfg.bg[k];
+  tgs_status s = launch_raster_tc_batch(rf, count, S->cfg.tiling.group_w, S->cfg.tiling.group_h, o,
+                                        b.counter, kReadyWaitNs, S->batch_stream);
+  if (s != TGS_OK) {
+    b.slots.clear();
+    return s;
   }
-  finish(S, sl, need > sl.bins_cap ? TGS_ERR_CAPACITY : TGS_OK);
+  for (int k : b.slots) {
+    S->slots[k].state = SlotState::kRaster;
+    S->slots[k].batch = bi;
+  }
+  TGS_CUDA(cudaEventRecord(b.done, S->batch_stream));
+  b.busy = true;
+  return TGS_OK;
 }
 
 void worker_main(tgs_server* S) {
@@ -289,37 +288,86 @@ void worker_main(tgs_server* S) {
   while (true) {
     bool progress = false, any_busy = false;
     const auto now = Clock::now();
+    // frames whose last tile group the batched launch has rendered
     for (Slot& sl : S->slots) {
-      if (!sl.busy) continue;
-      const cudaError_t q = cudaEventQuery(sl.done);
-      if (q == cudaSuccess) {
-        on_done(S, sl);
-        progress = true;
-      } else if (q != cudaErrorNotReady) {
-        cuda_status(q, "serving frame");
-        finish(S, sl, TGS_ERR_CUDA);
-        progress = true;
-      } else if (!sl.timed_out && S->core.expired(sl.req, now)) {
+      if (sl.state != SlotState::kRaster || host_word(&sl.host->done) != sl.seq) continue;
+      finish(S, sl, host_word(&sl.host->status) == TGS_OK ? TGS_OK : TGS_ERR_TIMEOUT);
+      progress = true;
+    }
+    // batched launches that ended: any frame of theirs not reported done failed (a CTA gave up)
+    for (int bi = 0; bi < kMaxBatches; ++bi) {
+      Batch& b = S->batches[bi];
+      if (!b.busy) continue;
+      const cudaError_t q = cudaEventQuery(b.done);
+      if (q == cudaErrorNotReady) continue;
+      for (int k : b.slots) {
+        Slot& sl = S->slots[k];
+        if (sl.state != SlotState::kRaster || sl.batch != bi) continue;
+        if (q != cudaSuccess) {
+          cuda_status(q, "batched rasterization");
+          finish(S, sl, TGS_ERR_CUDA);
+        } else {
+          const bool ok = host_word(&sl.host->done) == sl.seq && host_word(&sl.host->status) == TGS_OK;
+          finish(S, sl, ok ? TGS_OK : TGS_ERR_TIMEOUT);
+        }
+      }
+      b.busy = false;
+      b.slots.clear();
+      progress = true;
+    }
+    // slots whose binning (or FP32 frame) completed
+    for (Slot& sl : S->slots) {
+      if (sl.state == SlotState::kFree) continue;
+      any_busy = true;
+      if (sl.state == SlotState::kBinning) {
+        const cudaError_t q = cudaEventQuery(sl.done);
+        if (q == cudaSuccess) {
+          const tgs_status st = binning_status(S, sl);
+          if (st != TGS_OK || !S->tensor_cores() || sl.timed_out)
+            finish(S, sl, st);
+          else
+            sl.state = SlotState::kReady;
+          progress = true;
+        } else if (q != cudaErrorNotReady) {
+          cuda_status(q, "serving frame");
+          finish(S, sl, TGS_ERR_CUDA);
+          progress = true;
+        }
+      }
+      if (sl.state != SlotState::kFree && !sl.timed_out && S->core.expired(sl.req, now)) {
         S->core.complete(sl.req.ticket, TGS_ERR_TIMEOUT);  // the slot stays busy until the GPU is done
         sl.timed_out = true;
       }
-      any_busy |= sl.busy;
     }
     const bool stopping = S->core.stopping();
     if (!stopping) {
       for (Slot& sl : S->slots) {
-        if (sl.busy) continue;
+        if (sl.state != SlotState::kFree) continue;
         Request r;
         if (!S->core.next(&r)) break;
         sl.req = r;
-        sl.busy = true;
         sl.timed_out = false;
         const tgs_status s = issue(S, sl);
         if (s != TGS_OK) finish(S, sl, s);
-        any_busy |= sl.busy;
+        any_busy |= sl.state != SlotState::kFree;
         progress = true;
       }
-    } else {
+    }
+    // one persistent launch over every binned frame, if a launch slot is free
+    bool ready = false;
+    for (Slot& sl : S->slots) ready |= sl.state == SlotState::kReady;
+    if (ready) {
+      for (int bi = 0; bi < kMaxBatches; ++bi) {
+        if (S->batches[bi].busy) continue;
+        const tgs_status s = launch_batch(S, bi);
+        if (s != TGS_OK)
+          for (Slot& sl : S->slots)
+            if (sl.state == SlotState::kReady) finish(S, sl, s);
+        progress = true;
+        break;
+      }
+    }
+    if (stopping) {
       if (!any_busy) break;
       if (stop_seen == Clock::time_point{}) stop_seen = now;
       if (now - stop_seen > std::chrono::milliseconds(kDrainLimitMs)) {
@@ -370,31 +418,60 @@ tgs_status tgs_serve_create(const tgs_serve_config* config, tgs_server** out) {
        c.precision != TGS_PRECISION_BF16_TC) ||
       c.tiling.group_w < 1 || c.tiling.group_w > TGS_MAX_GROUP || c.tiling.group_h < 1 ||
       c.tiling.group_h > TGS_MAX_GROUP || (c.tiling.flags & ~TGS_BIN_RANGE_ONLY) != 0 ||
-      c.request_timeout_ms < 0)
+      c.request_timeout_ms < 0 || c.max_gaussians < 1 || c.max_gaussians >= (int64_t(1) << 30) ||
+      c.max_width < 1 || c.max_width > 16384 || c.max_height < 1 || c.max_height > 16384 ||
+      c.max_entries < 1 || c.max_entries >= (int64_t(1) << 30))
     return set_error("bad serving config"), TGS_ERR_INVALID_ARGUMENT;
   tgs_status s = tgs_check_device(c.device);
   if (s != TGS_OK) return s;
   DeviceGuard guard(c.device);
   TGS_CUDA(guard.status);
-  int32_t* err = device_error_word();
-  if (!err) return set_error("device error word unavailable"), TGS_ERR_CUDA;
   auto* S = new tgs_server(c);
-  S->err_word = err;
+  S->slot_bytes = slot_layout(c, nullptr);
+  const size_t batch_bytes = 256 * kMaxBatches;
+  const size_t total = S->slot_bytes * (size_t)c.slots + batch_bytes;
+  if (!S->reserve(total)) {
+    set_error("%d slots of %zu bytes exceed the serving budget of %lld bytes", c.slots, S->slot_bytes,
+              (long long)c.hbm_budget_bytes);
+    delete S;
+    return TGS_ERR_CAPACITY;
+  }
+  // stream priorities: the slots' short binning kernels take SM slots as the batched launch's CTAs
+  // retire, instead of queueing behind it
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  auto cleanup = [&](cudaError_t e, const char* what) {
+    for (Slot& t : S->slots) {
+      if (t.stream) cudaStreamDestroy(t.stream);
+      if (t.done) cudaEventDestroy(t.done);
+      if (t.host) cudaFreeHost(t.host);
+      if (t.mem) cudaFree(t.mem);
+    }
+    for (Batch& b : S->batches)
+      if (b.done) cudaEventDestroy(b.done);
+    if (S->batch_stream) cudaStreamDestroy(S->batch_stream);
+    if (S->batch_mem) cudaFree(S->batch_mem);
+    delete S;
+    return cuda_status(e, what);
+  };
   S->slots.resize(c.slots);
   for (Slot& sl : S->slots) {
-    cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    cudaError_t e = cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking, hi);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = pinned_malloc(reinterpret_cast<void**>(&sl.host), sizeof(Readback));
-    if (e != cudaSuccess) {
-      for (Slot& t : S->slots) {
-        if (t.stream) cudaStreamDestroy(t.stream);
-        if (t.done) cudaEventDestroy(t.done);
-        if (t.host) cudaFreeHost(t.host);
-      }
-      delete S;
-      return cuda_status(e, "serving slot");
-    }
+    if (e == cudaSuccess) e = device_malloc(&sl.mem, S->slot_bytes);
+    if (e != cudaSuccess) return cleanup(e, "serving slot");
+    slot_layout(c, &sl);
+    e = cudaMemset(sl.words, 0, 16);
+    if (e != cudaSuccess) return cleanup(e, "serving slot");
   }
+  cudaError_t e = cudaStreamCreateWithPriority(&S->batch_stream, cudaStreamNonBlocking, lo);
+  if (e == cudaSuccess) e = device_malloc(&S->batch_mem, batch_bytes);
+  for (int k = 0; e == cudaSuccess && k < kMaxBatches; ++k) {
+    e = cudaEventCreateWithFlags(&S->batches[k].done, cudaEventDisableTiming);
+    S->batches[k].counter = reinterpret_cast<int*>(static_cast<char*>(S->batch_mem) + 256 * k);
+  }
+  if (e != cudaSuccess) return cleanup(e, "serving batch stream");
   S->worker = std::thread(worker_main, S);
   *out = S;
   return TGS_OK;
@@ -411,6 +488,11 @@ tgs_status tgs_serve_add_scene(tgs_server* S, const tgs_scene* scene, int32_t* s
   const size_t b_means = a256(12 * n), b_scales = a256(12 * n), b_quats = a256(16 * n),
                b_opac = a256(4 * n), b_sh = a256(12 * k * n);
   const size_t bytes = std::max<size_t>(256, b_means + b_scales + b_quats + b_opac + b_sh);
+  if (n > S->cfg.max_gaussians) {
+    set_error("a scene of %lld Gaussians exceeds the slots' %lld", (long long)n,
+              (long long)S->cfg.max_gaussians);
+    return TGS_ERR_CAPACITY;
+  }
   if (!S->reserve(bytes)) {
     set_error("serving budget of %lld bytes exceeded by a scene of %zu bytes",
               (long long)S->cfg.hbm_budget_bytes, bytes);
@@ -515,7 +597,7 @@ tgs_status tgs_serve_pause(tgs_server* S, int32_t paused) {
 tgs_status tgs_serve_get_stats(tgs_server* S, tgs_serve_stats* out) {
   if (!S || !out) return set_error("null argument"), TGS_ERR_INVALID_ARGUMENT;
   S->core.stats(out);
-  out->regrown = S->regrown.load();
+  out->regrown = 0;
   out->hbm_bytes = S->hbm.load();
   return TGS_OK;
 }
@@ -528,14 +610,18 @@ tgs_status tgs_serve_destroy(tgs_server* S) {
   const bool drained = S->drained.load();
   for (Slot& sl : S->slots) {
     if (drained) {  // else frames may still write to these buffers: they are left allocated
-      free_slot_buffers(S, sl);
+      cudaFree(sl.mem);
       cudaFreeHost(sl.host);
     }
     cudaStreamDestroy(sl.stream);
     cudaEventDestroy(sl.done);
   }
-  if (drained)
+  for (Batch& b : S->batches) cudaEventDestroy(b.done);
+  cudaStreamDestroy(S->batch_stream);
+  if (drained) {
+    cudaFree(S->batch_mem);
     for (auto& kv : S->scenes) cudaFree(kv.second.mem);
+  }
   delete S;
   if (!drained)
     return set_error("frames still running after %d ms: their device memory was not freed",

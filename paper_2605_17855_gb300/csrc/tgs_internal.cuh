@@ -45,9 +45,10 @@ inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 tgs_status launch_preprocess(const tgs_scene& s, const tgs_camera& cam, const tgs_projected& out,
                              cudaStream_t st);
 size_t bin_sort_workspace_bytes(int64_t n, int64_t capacity, int GX, int GY);
+// err_word: the device word its bounded waits report to (NULL: the library's error word).
 tgs_status launch_bin_sort(const tgs_projected& p, int64_t n, int width, int height, int gw, int gh,
                            bool membership, void* ws, size_t ws_bytes, const tgs_bins& bins,
-                           cudaStream_t st);
+                           cudaStream_t st, int32_t* err_word = nullptr);
 tgs_status launch_raster_fp32(const tgs_projected& p, const tgs_bins& b, int width, int height,
                               int gw, int gh, const tgs_raster_opts& o, float* out_rgb, float* out_T,
                               int32_t* n_contrib, cudaStream_t st);
@@ -67,6 +68,8 @@ struct RasterFrame {
   const int32_t* ready;
   int32_t ready_value;
   int32_t* status;
+  int32_t* done;
+  int32_t done_value;
 };
 tgs_status launch_raster_tc_batch(const RasterFrame* frames, int count, int gw, int gh,
                                   const tgs_raster_opts& o, int* next_item, uint64_t wait_ns,

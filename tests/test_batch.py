@@ -69,6 +69,7 @@ def test_ready_flags_and_device_timeout(frames_src):
     prepared = _prepare(ds, views[:3], (2, 2))
     ready = torch.zeros(3, dtype=torch.int32, device="cuda")
     status = torch.zeros(3, dtype=torch.int32, device="cuda")
+    done = torch.zeros(3, dtype=torch.int32).pin_memory()  # host words the device writes
     ready[0] = 5
     ready[2] = 5  # frame 1's flag is never set
     frames, refs = [], []
@@ -76,20 +77,24 @@ def test_ready_flags_and_device_timeout(frames_src):
         rgb = torch.full((3, cam.height, cam.width), -1.0, device="cuda")
         T = torch.full((cam.height, cam.width), -1.0, device="cuda")
         frames.append(tgs.BatchFrame(proj, bins, cam.width, cam.height, rgb, T, ready=ready[k:k + 1],
-                                     ready_value=5, status=status[k:k + 1]))
+                                     ready_value=5, status=status[k:k + 1], done=done[k:k + 1],
+                                     done_value=10 + k))
         refs.append(tgs.rasterize(proj, bins, cam.width, cam.height, "fp16_tc", want_n_contrib=False))
     ws = tgs.rasterize_batch(frames, (2, 2), "fp16_tc", wait_limit_ns=2_000_000)  # 2 ms
     torch.cuda.synchronize()
     assert _np(status).tolist() == [tgs.TGS_OK, tgs.TGS_ERR_TIMEOUT, tgs.TGS_OK]
+    assert done.tolist() == [10, 11, 12]  # every frame completes, the failed one included
     for k in (0, 2):
         assert np.array_equal(_np(frames[k].out_rgb), _np(refs[k][0]))
     assert np.all(_np(frames[1].out_rgb) == -1.0)  # skipped: nothing written
     # the device stays usable: once the flag is set the same batch renders every frame
     ready[1] = 5
     status.zero_()
+    done.zero_()
     tgs.rasterize_batch(frames, (2, 2), "fp16_tc", workspace=ws)
     torch.cuda.synchronize()
     assert _np(status).tolist() == [0, 0, 0] and tgs.last_device_error() == 0
+    assert done.tolist() == [10, 11, 12]
     for f, r in zip(frames, refs):
         assert np.array_equal(_np(f.out_rgb), _np(r[0]))
 

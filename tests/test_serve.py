@@ -1,6 +1,8 @@
-"""GPU tests of the rendering service (tgs_serve_*): frames rendered by the server equal the direct
-preprocess -> bin sort -> rasterize path bit for bit; admission (BUSY), pause, bounded waits,
-scene removal while in use, the HBM budget, bin capacity growth and per-resolution statistics."""
+"""GPU tests of the rendering service (tgs_serve_*): frames rendered by the server (binned per slot,
+rasterized together by batched tensor-core launches) equal the direct preprocess -> bin sort ->
+rasterize path bit for bit; admission (BUSY), pause, bounded waits, scene removal while in use, the
+fixed slot capacities and the HBM budget, nothing allocated by the worker, and per-resolution
+statistics."""
 import numpy as np
 import pytest
 import torch
@@ -95,30 +97,46 @@ def test_admission_pause_wait_and_scene_removal():
         assert e.value.status == tgs.TGS_ERR_NOT_FOUND
 
 
-def test_budget_limits():
+def test_budget_and_slot_capacities():
     box, cam1, mix = _scenes()
-    # the mixture scene (60k Gaussians at SH degree 3) needs ~14 MB: too much for 4 MB
-    with tgs.Server(4 << 20, max_inflight=4, slots=1) as srv:
+    # slot buffers are allocated at creation: a budget that cannot hold them refuses the server
+    with pytest.raises(tgs.TgsError) as e:
+        tgs.Server(4 << 20, max_inflight=4, slots=2, max_gaussians=1 << 20, max_size=(2048, 2048))
+    assert e.value.status == tgs.TGS_ERR_CAPACITY
+    with tgs.Server(16 << 20, max_inflight=4, slots=1, max_gaussians=4096, max_size=(256, 256),
+                    max_entries=20000) as srv:
         with pytest.raises(tgs.TgsError) as e:
-            srv.add_scene(mix)
+            srv.add_scene(mix)  # 60k Gaussians: more than a slot renders
         assert e.value.status == tgs.TGS_ERR_CAPACITY
-        sid = srv.add_scene(box)  # 2,000 Gaussians fit
-        big = scenes.identity_camera(4096, 4096)  # its bins and workspace do not
-        rgb = torch.empty((3, 4096, 4096), device="cuda")
-        t = srv.submit(sid, big, rgb)
-        assert srv.wait(t, 20000) == tgs.TGS_ERR_CAPACITY
+        sid = srv.add_scene(box)
+        big = scenes.identity_camera(512, 512)  # larger than a slot's frame
+        rgb = torch.empty((3, 512, 512), device="cuda")
+        assert srv.wait(srv.submit(sid, big, rgb), 20000) == tgs.TGS_ERR_CAPACITY
+        rgb = torch.empty((3, cam1.height, cam1.width), device="cuda")
+        assert srv.wait(srv.submit(sid, cam1, rgb), 20000) == tgs.TGS_OK
         assert srv.stats()["failed"] == 1
 
 
-def test_capacity_growth_renders_again():
-    # 1x1 tiles and large splats: more than 4 entries per Gaussian, so the first frame of a slot
-    # overflows its initial capacity and is rendered again
-    scene = scenes.box_scene(3000, seed=3, log_scale_mean=-1.8)
-    cam = scenes.identity_camera(256, 256)
-    with tgs.Server(2 * GB, max_inflight=4, slots=1, tiling=(1, 1)) as srv:
-        sid = srv.add_scene(scene)
-        rgb = torch.empty((3, 256, 256), device="cuda")
-        assert srv.wait(srv.submit(sid, cam, rgb), 20000) == tgs.TGS_OK
-        assert srv.stats()["regrown"] >= 1
-        ref, _ = _direct(tgs.DeviceScene.from_host(scene), cam, (1, 1), "fp16_tc")
-        assert np.array_equal(rgb.cpu().numpy(), ref)
+def test_entry_capacity_and_no_allocation_in_the_worker():
+    # a frame that needs more bin entries than the slot holds completes with CAPACITY; the server
+    # allocates nothing while it renders (every buffer comes from tgs_serve_create / add_scene)
+    box, cam1, _ = _scenes()
+    lib = tgs.load()
+    with tgs.Server(1 << 30, max_inflight=8, slots=2, max_gaussians=4096, max_size=(128, 128),
+                    max_entries=500) as srv:
+        sid = srv.add_scene(box)
+        before = lib.tgs_allocation_count()
+        rgb = torch.empty((3, cam1.height, cam1.width), device="cuda")
+        assert srv.wait(srv.submit(sid, cam1, rgb), 20000) == tgs.TGS_ERR_CAPACITY
+        assert lib.tgs_allocation_count() == before
+    with tgs.Server(1 << 30, max_inflight=8, slots=2, max_gaussians=4096, max_size=(128, 128),
+                    max_entries=20000) as srv:
+        sid = srv.add_scene(box)
+        before = lib.tgs_allocation_count()
+        bufs = [torch.empty((3, cam1.height, cam1.width), device="cuda") for _ in range(6)]
+        for t in [srv.submit(sid, cam1, b) for b in bufs]:
+            assert srv.wait(t, 20000) == tgs.TGS_OK
+        assert lib.tgs_allocation_count() == before
+        ref, _ = _direct(tgs.DeviceScene.from_host(box), cam1, (2, 2), "fp16_tc")
+        for b in bufs:
+            assert np.array_equal(b.cpu().numpy(), ref)
