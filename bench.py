@@ -250,10 +250,15 @@ def run_dense4k(args):
                 raise RuntimeError("bin capacity overflow")
             del rend
             torch.cuda.empty_cache()
-    rend = tgs.Renderer(ds, cams, (1, 1), "fp32")
+    # the plain FP32 tile rasterizer (AABB-range lists), and FP32 on the membership lists
+    rend = tgs.Renderer(ds, cams, (1, 1), "fp32", membership=False)
     table["fp32_1x1"] = round(_time_renderer(rend, len(cams), steps, 3), 4)
     del rend
+    rend = tgs.Renderer(ds, cams, (1, 1), "fp32")
+    table["fp32_1x1_membership"] = round(_time_renderer(rend, len(cams), steps, 3), 4)
+    del rend
     best = {p: min((v, k) for k, v in table.items() if k.startswith(p)) for p in ("fp16_tc", "bf16_tc")}
+    torch.cuda.empty_cache()
     errors = {}
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -267,6 +272,8 @@ def run_dense4k(args):
                             "psnr_db": round(oracle.psnr(got, ref), 2),
                             "max_abs": float(np.abs(got - ref).max())}
     px = len(cams) * W * H
+    del ds
+    torch.cuda.empty_cache()
     out = {"metric": "rasterize Mpx/s, grouping x precision autotune (6M Gaussians, 3840x2160)",
            "value": round(W * H / (best["fp16_tc"][0] * 1e-3) / 1e6, 2), "unit": "Mpx/s", "n_gpus": ws,
            "higher_is_better": True, "dtype": DTYPE["fp16_tc"], "data": "synthetic",
@@ -276,6 +283,8 @@ def run_dense4k(args):
            "autotune": {p: {"tiling": k.split("_")[-1], "frame_ms": v} for p, (v, k) in best.items()},
            "speedup_vs_fp32_core": round(table["fp32_1x1"] / best["fp16_tc"][0], 3),
            "error_vs_oracle": errors}
+    if getattr(args, "return_dict", False):
+        return out
     if rank == 0:
         print(json.dumps(out))
     return 0
@@ -331,6 +340,10 @@ def run_backward(args):
            "config": {"workload": "500k Gaussians (box generator, SH degree 0), 8 yaw-jittered cameras at "
                                   "1024x1024, 2x2 groups", "steps": steps},
            "ms_per_step": round(ms, 4), "backward_ms_per_frame": round(bwd_ms, 4)}
+    del frames, ds
+    torch.cuda.empty_cache()
+    if getattr(args, "return_dict", False):
+        return out
     if rank == 0:
         print(json.dumps(out))
     return 0
@@ -550,6 +563,8 @@ def main():
     ap.add_argument("--tiling", default="2x2")
     ap.add_argument("--splats", type=int, default=1_500_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-workloads", action="store_true",
+                    help="skip the 4K autotune, backward and serving workloads appended to the headline line")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     ap.add_argument("--ref-sample-s", type=float, default=8.0)
     ap.add_argument("--workload", default="frames", choices=["frames", "dense4k", "backward"],
@@ -834,6 +849,26 @@ def main():
         rec, psnr = cpu_baseline(scene, cams[0], tc_image=rgb.cpu().numpy(), target_s=args.cpu_sample_s)
         out["cpu_baseline"] = rec
         out["psnr_vs_oracle_sampled"] = round(psnr, 3) if psnr is not None and math.isfinite(psnr) else psnr
+    if ws == 1 and not args.no_extra_workloads:
+        # the other workloads of the evaluation, in the same run: 6M Gaussians at 3840x2160 (grouping
+        # x precision autotune with its error against the oracle), forward + backward, and the
+        # rendering service under a sweep of offered rates
+        del R, rs, e_proj, e_bins, e_out, ds
+        torch.cuda.empty_cache()
+        import argparse as _ap
+        sub = _ap.Namespace(**vars(args))
+        sub.return_dict = True
+        sub.steps = 5
+        sub.cpu_sample_s = 6.0
+        extra = {"dense4k": run_dense4k(sub)}
+        torch.cuda.empty_cache()
+        extra["backward"] = run_backward(sub)
+        torch.cuda.empty_cache()
+        rates = [float(r) for r in args.rates.split(",")]
+        res, hbm = serve_sweep(rates, 2.0, args.precision, tiling, local)
+        extra["serve"] = {"metric": "serve frames/s & p50/p99 latency per resolution (4 resident scenes)",
+                          "seconds_per_rate": 2.0, "rates": res, "hbm_bytes": hbm}
+        out["workloads"] = extra
     if rank == 0:
         print(json.dumps(out))
     if dist:
