@@ -39,8 +39,10 @@ constexpr int kSortThreads = 256;  // 8 warps
 constexpr int kSortItems = 16;     // per thread
 constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 items per tile
 constexpr int kMaxPasses = 4;
-// items per thread of the radix passes (tiles of 256 x items)
+// threads and items per thread of the radix passes (tiles of threads x items)
+constexpr int kDepthThreads = 256;
 constexpr int kDepthItems = 16;
+constexpr int kGidThreads = 256;
 constexpr int kGidItems = 16;
 // Look-back status words: 2 flag bits over a 30-bit count (sizes are limited to < 2^30).
 constexpr uint32_t kFlagAgg = 1u << 30;     // the tile's own count is published
@@ -68,8 +70,9 @@ __device__ __forceinline__ T warp_incl_scan(T v) {
   return v;
 }
 
-// Exclusive scan over the block's 256 threads (all of them call it); `tmp` holds 8 values.
-template <typename T>
+// Exclusive scan over the block's THREADS threads (all of them call it); `tmp` holds THREADS / 32
+// values.
+template <typename T, int THREADS = kSortThreads>
 __device__ __forceinline__ T block_excl_scan(T v, T* tmp, T* total = nullptr) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const T incl = warp_incl_scan(v);
@@ -78,7 +81,7 @@ __device__ __forceinline__ T block_excl_scan(T v, T* tmp, T* total = nullptr) {
   __syncthreads();
   T add = 0, all = 0;
 #pragma unroll
-  for (int w = 0; w < kSortThreads / 32; ++w) {
+  for (int w = 0; w < THREADS / 32; ++w) {
     const T t = tmp[w];
     if (w < warp) add += t;
     all += t;
@@ -402,28 +405,40 @@ __device__ __forceinline__ uint32_t lanes_sum(uint32_t S, uint32_t lo_k, uint32_
 // global start of the digit plus the counts of that digit in the earlier tiles (look-back). Items
 // are staged in shared memory in digit order and written so that each digit's run is contiguous
 // and consecutive threads store consecutive words.
-// With MASK, a 16-bit payload (the entry's tile mask) travels with each item as well.
-template <int ITEMS, bool MASK>
-__global__ void __launch_bounds__(kSortThreads) k_onesweep(
+// With MASK, a 16-bit payload (the entry's tile mask) travels with each item as well. THREADS is a
+// multiple of the 256 digits: the first 256 threads also do the per-digit work. Larger tiles mean
+// fewer tiles, hence a shorter look-back chain when all tiles run in one wave. The staging buffers
+// are dynamic shared memory (onesweep_smem_bytes).
+template <int THREADS, int ITEMS, bool MASK>
+constexpr size_t onesweep_smem_bytes() {
+  return (size_t)THREADS * ITEMS * (8 + (MASK ? 2 : 0));
+}
+
+template <int THREADS, int ITEMS, bool MASK>
+__global__ void __launch_bounds__(THREADS) k_onesweep(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     const uint16_t* __restrict__ masks_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, uint16_t* __restrict__ masks_out, const int64_t* count_dev,
     int64_t count_host, int64_t cap, int shift, const uint32_t* __restrict__ ghist,
     uint32_t* __restrict__ status, int* __restrict__ tile_counter, int32_t* __restrict__ err) {
-  constexpr int W = kSortThreads / 32;
+  static_assert(THREADS % kRadix == 0, "THREADS must be a multiple of the digit count");
+  constexpr int W = THREADS / 32;
+  constexpr int TILE = THREADS * ITEMS;
   __shared__ uint32_t wcount[W][kRadix];  // per warp and digit: count, then exclusive offset
   __shared__ uint32_t dstart[kRadix];     // tile-local start of each digit's run
   __shared__ uint32_t boff[kRadix];       // global start of this tile's run of each digit
   __shared__ uint32_t tmp[W];
-  __shared__ uint32_t skey[kSortThreads * ITEMS], sval[kSortThreads * ITEMS];
-  __shared__ uint16_t smask[MASK ? kSortThreads * ITEMS : 1];
+  extern __shared__ __align__(16) uint8_t stage_raw[];
+  uint32_t* skey = reinterpret_cast<uint32_t*>(stage_raw);
+  uint32_t* sval = skey + TILE;
+  uint16_t* smask = reinterpret_cast<uint16_t*>(sval + TILE);
   __shared__ int s_tile;
   if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1);
-  for (int k = threadIdx.x; k < W * kRadix; k += kSortThreads) (&wcount[0][0])[k] = 0;
+  for (int k = threadIdx.x; k < W * kRadix; k += THREADS) (&wcount[0][0])[k] = 0;
   __syncthreads();
   const int tile = s_tile;
   const int64_t count = live_count(count_dev, count_host, cap);
-  const int64_t block_base = (int64_t)tile * (kSortThreads * ITEMS);
+  const int64_t block_base = (int64_t)tile * TILE;
   if (block_base >= count) return;  // uniform per block; later tickets are past the end too
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
@@ -456,21 +471,25 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     rank[r] = base + before;
   }
   __syncthreads();
-  // per digit (one thread each): exclusive offsets over warps and the tile total
-  static_assert(kSortThreads == kRadix, "one thread per digit");
+  // per digit (the first 256 threads, one each): exclusive offsets over warps and the tile total
   const int d = threadIdx.x;
+  const bool digit_thread = d < kRadix;
   uint32_t total = 0;
-#pragma unroll
-  for (int w = 0; w < W; ++w) {
-    const uint32_t c = wcount[w][d];
-    wcount[w][d] = total;
-    total += c;
+  if (digit_thread) {
+#pragma unroll 8
+    for (int w = 0; w < W; ++w) {
+      const uint32_t c = wcount[w][d];
+      wcount[w][d] = total;
+      total += c;
+    }
   }
-  const uint32_t excl_tiles = lookback32(status, tile, kRadix, d, total, err);
-  const uint32_t gstart = block_excl_scan<uint32_t>(ghist[d], tmp);
-  const uint32_t ds = block_excl_scan<uint32_t>(total, tmp);
-  dstart[d] = ds;
-  boff[d] = gstart + excl_tiles;
+  const uint32_t excl_tiles = digit_thread ? lookback32(status, tile, kRadix, d, total, err) : 0u;
+  const uint32_t gstart = block_excl_scan<uint32_t, THREADS>(digit_thread ? ghist[d] : 0u, tmp);
+  const uint32_t ds = block_excl_scan<uint32_t, THREADS>(total, tmp);
+  if (digit_thread) {
+    dstart[d] = ds;
+    boff[d] = gstart + excl_tiles;
+  }
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
@@ -479,20 +498,36 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
       const uint32_t p = dstart[dd] + wcount[warp][dd] + rank[r];
       skey[p] = key[r];
       sval[p] = val[r];
-      if (MASK) smask[MASK ? p : 0] = msk[MASK ? r : 0];
+      if (MASK) smask[p] = msk[MASK ? r : 0];
     }
   }
   __syncthreads();
-  const int nvalid = (int)min((int64_t)(kSortThreads * ITEMS), count - block_base);
-  for (int i = threadIdx.x; i < nvalid; i += kSortThreads) {
+  const int nvalid = (int)min((int64_t)TILE, count - block_base);
+  for (int i = threadIdx.x; i < nvalid; i += THREADS) {
     const uint32_t k = skey[i];
     const int dd = (int)((k >> shift) & (kRadix - 1));
     const uint32_t pos = boff[dd] + (uint32_t)i - dstart[dd];
     if (pos >= (uint32_t)count) continue;  // only after an expired look-back (offsets then short)
     keys_out[pos] = k;
     vals_out[pos] = sval[i];
-    if (MASK) masks_out[pos] = smask[MASK ? i : 0];
+    if (MASK) masks_out[pos] = smask[i];
   }
+}
+
+// Launches one radix pass with the tiling of THREADS x ITEMS items per tile.
+template <int THREADS, int ITEMS, bool MASK>
+tgs_status launch_onesweep(int blocks, cudaStream_t st, const uint32_t* keys_in, const uint32_t* vals_in,
+                           const uint16_t* masks_in, uint32_t* keys_out, uint32_t* vals_out,
+                           uint16_t* masks_out, const int64_t* count_dev, int64_t cap, int shift,
+                           const uint32_t* ghist, uint32_t* status, int* tile_counter, int32_t* err) {
+  constexpr size_t smem = onesweep_smem_bytes<THREADS, ITEMS, MASK>();
+  auto* k = k_onesweep<THREADS, ITEMS, MASK>;
+  // static + dynamic shared memory may exceed the default 48 KB: opt in to the dynamic part
+  TGS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k<<<blocks, THREADS, smem, st>>>(keys_in, vals_in, masks_in, keys_out, vals_out, masks_out,
+                                   count_dev, 0, cap, shift, ghist, status, tile_counter, err);
+  TGS_CHECK_LAUNCH("k_onesweep");
+  return TGS_OK;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -805,8 +840,8 @@ WsLayout layout(int64_t n, int64_t cap, int GX, int GY) {
     return o;
   };
   L.nb_c = (int)std::max<int64_t>(1, div_up(n, kSortTile));
-  L.nb_d = (int)std::max<int64_t>(1, div_up(n, kSortThreads * kDepthItems));
-  L.nb_g = (int)std::max<int64_t>(1, div_up(cap, kSortThreads * kGidItems));
+  L.nb_d = (int)std::max<int64_t>(1, div_up(n, kDepthThreads * kDepthItems));
+  L.nb_g = (int)std::max<int64_t>(1, div_up(cap, kGidThreads * kGidItems));
   L.nb_o = L.nb_c;
   const int gpasses = std::max(1, div_up(group_bits(G), kRadixBits));
   L.dkA = take(4 * (size_t)n);
@@ -892,11 +927,11 @@ tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int h
   TGS_CHECK_LAUNCH("k_depth_keys");
   for (int pass = 0; pass < 4; ++pass) {
     const bool odd = pass & 1;
-    k_onesweep<kDepthItems, false><<<L.nb_d, kSortThreads, 0, st>>>(
-        odd ? dkB : dkA, odd ? dvB : dvA, nullptr, odd ? dkA : dkB, odd ? dvA : dvB, nullptr,
-        visible, 0, n, 8 * pass, hist_d + pass * kRadix, stat_d + (size_t)pass * L.nb_d * kRadix,
-        tickets + pass, err);
-    TGS_CHECK_LAUNCH("k_onesweep");
+    const tgs_status s = launch_onesweep<kDepthThreads, kDepthItems, false>(
+        L.nb_d, st, odd ? dkB : dkA, odd ? dvB : dvA, nullptr, odd ? dkA : dkB, odd ? dvA : dvB,
+        nullptr, visible, n, 8 * pass, hist_d + pass * kRadix,
+        stat_d + (size_t)pass * L.nb_d * kRadix, tickets + pass, err);
+    if (s != TGS_OK) return s;
   }
   const uint32_t* order = dvA;  // after an even number of passes
 
@@ -935,11 +970,11 @@ tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int h
   const uint32_t* gk = ek;
   for (int pass = 0; pass < passes; ++pass) {
     const bool odd = pass & 1;
-    k_onesweep<kGidItems, true><<<L.nb_g, kSortThreads, 0, st>>>(
-        odd ? ok : ek, odd ? ov : ev, odd ? om : em, odd ? ek : ok, odd ? ev : ov, odd ? em : om,
-        b.num_entries, 0, cap, 8 * pass, hist_g + pass * kRadix,
+    const tgs_status s = launch_onesweep<kGidThreads, kGidItems, true>(
+        L.nb_g, st, odd ? ok : ek, odd ? ov : ev, odd ? om : em, odd ? ek : ok, odd ? ev : ov,
+        odd ? em : om, b.num_entries, cap, 8 * pass, hist_g + pass * kRadix,
         stat_g + (size_t)pass * L.nb_g * kRadix, tickets + 4 + pass, err);
-    TGS_CHECK_LAUNCH("k_onesweep");
+    if (s != TGS_OK) return s;
     gk = odd ? ek : ok;
   }
 
