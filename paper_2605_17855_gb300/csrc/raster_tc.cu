@@ -14,10 +14,11 @@ tgs_status launch_raster_tc(const tgs_projected& p, const tgs_bins& b, int width
 
 tgs_status launch_raster_tc_batch(const RasterFrame* frames, int count, int gw, int gh,
                                   const tgs_raster_opts& o, int* next_item, uint64_t wait_ns,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, int share_div) {
   if (o.precision == TGS_PRECISION_BF16_TC)
-    return launch_raster_tc_batch_bf16(frames, count, gw, gh, o, next_item, wait_ns, st);
-  return launch_raster_tc_batch_typed<false>(frames, count, gw, gh, o, next_item, wait_ns, st);
+    return launch_raster_tc_batch_bf16(frames, count, gw, gh, o, next_item, wait_ns, st, share_div);
+  return launch_raster_tc_batch_typed<false>(frames, count, gw, gh, o, next_item, wait_ns, st,
+                                             share_div);
 }
 
 }  // namespace tgs

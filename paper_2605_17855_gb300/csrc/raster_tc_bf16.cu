@@ -13,8 +13,9 @@ tgs_status launch_raster_tc_bf16(const tgs_projected& p, const tgs_bins& b, int 
 
 tgs_status launch_raster_tc_batch_bf16(const RasterFrame* frames, int count, int gw, int gh,
                                        const tgs_raster_opts& o, int* next_item, uint64_t wait_ns,
-                                       cudaStream_t st) {
-  return launch_raster_tc_batch_typed<true>(frames, count, gw, gh, o, next_item, wait_ns, st);
+                                       cudaStream_t st, int share_div) {
+  return launch_raster_tc_batch_typed<true>(frames, count, gw, gh, o, next_item, wait_ns, st,
+                                            share_div);
 }
 
 }  // namespace tgs

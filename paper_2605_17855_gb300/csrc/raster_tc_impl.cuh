@@ -1057,7 +1057,7 @@ tgs_status launch_raster_tc_typed(const tgs_projected& p, const tgs_bins& b, int
 
 template <bool BF, int GW, int GH, int NWG, int NPROD, int NST = 2>
 tgs_status launch_batch_cfg(const RasterFrame* frames, int count, const tgs_raster_opts& o,
-                            int* next_item, uint64_t wait_ns, cudaStream_t st) {
+                            int* next_item, uint64_t wait_ns, cudaStream_t st, int share_div) {
   using Cf = Cfg<GW, GH, NWG, NPROD, NST>;
   using Sm = Smem<GW * GH, Cf::kSlots, BF ? 2 : 1>;
   BatchArgs B{};
@@ -1104,7 +1104,8 @@ tgs_status launch_batch_cfg(const RasterFrame* frames, int count, const tgs_rast
   TGS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
   TGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, Cf::kThreads, smem));
-  const int grid = (int)std::min<int64_t>(std::max<int64_t>(total, 1), (int64_t)std::max(occ, 1) * sms);
+  const int64_t slots = std::max<int64_t>(1, (int64_t)std::max(occ, 1) * sms / std::max(share_div, 1));
+  const int grid = (int)std::min<int64_t>(std::max<int64_t>(total, 1), slots);
   TGS_CUDA(cudaMemsetAsync(next_item, 0, sizeof(int) * (1 + kMaxBatchFrames), st));
   const float3 bg = make_float3(o.bg[0], o.bg[1], o.bg[2]);
   const int cull = (o.flags & TGS_RASTER_NO_CULL) ? 0 : 1;
@@ -1116,14 +1117,14 @@ tgs_status launch_batch_cfg(const RasterFrame* frames, int count, const tgs_rast
 template <bool BF>
 tgs_status launch_raster_tc_batch_typed(const RasterFrame* frames, int count, int gw, int gh,
                                         const tgs_raster_opts& o, int* next_item, uint64_t wait_ns,
-                                        cudaStream_t st) {
+                                        cudaStream_t st, int share_div) {
   constexpr int NST = BF ? 2 : 1;  // the configurations of the single-frame launch
-  if (gw == 1 && gh == 1) return launch_batch_cfg<BF, 1, 1, 1, 2>(frames, count, o, next_item, wait_ns, st);
-  if (gw == 2 && gh == 2) return launch_batch_cfg<BF, 2, 2, 4, 3, NST>(frames, count, o, next_item, wait_ns, st);
-  if (gw == 4 && gh == 2) return launch_batch_cfg<BF, 4, 2, 4, 3, NST>(frames, count, o, next_item, wait_ns, st);
-  if (gw == 2 && gh == 4) return launch_batch_cfg<BF, 2, 4, 4, 3, NST>(frames, count, o, next_item, wait_ns, st);
+  if (gw == 1 && gh == 1) return launch_batch_cfg<BF, 1, 1, 1, 2>(frames, count, o, next_item, wait_ns, st, share_div);
+  if (gw == 2 && gh == 2) return launch_batch_cfg<BF, 2, 2, 4, 3, NST>(frames, count, o, next_item, wait_ns, st, share_div);
+  if (gw == 4 && gh == 2) return launch_batch_cfg<BF, 4, 2, 4, 3, NST>(frames, count, o, next_item, wait_ns, st, share_div);
+  if (gw == 2 && gh == 4) return launch_batch_cfg<BF, 2, 4, 4, 3, NST>(frames, count, o, next_item, wait_ns, st, share_div);
   if (gw == 4 && gh == 4)
-    return launch_batch_cfg<BF, 4, 4, 4, BF ? 2 : 3>(frames, count, o, next_item, wait_ns, st);
+    return launch_batch_cfg<BF, 4, 4, 4, BF ? 2 : 3>(frames, count, o, next_item, wait_ns, st, share_div);
   set_error("tensor-core path supports groups 1x1, 2x2, 4x2, 2x4, 4x4 (got %dx%d)", gw, gh);
   return TGS_ERR_INVALID_ARGUMENT;
 }

@@ -10,9 +10,10 @@
 // The worker moves queued requests into free slots and preprocesses and bins them there,
 // asynchronously on the slot's stream (frames of different scenes and resolutions overlap on the
 // GPU). With a tensor-core precision, the slots whose binning has finished are then rasterized
-// together by one persistent launch (tgs_rasterize_batch over (frame, tile group) work items) on
-// the batch stream; up to two launches are in flight, and requests that arrive meanwhile are binned
-// and join the next launch (continuous batching). The launch waits (bounded) on each slot's
+// together by one persistent launch (tgs_rasterize_batch over (frame, tile group) work items). Up
+// to two launches are in flight, each on its own stream with half of the GPU's CTA slots, so a
+// launch of newly binned frames starts beside a running one; requests that arrive meanwhile are
+// binned and join the next launch (continuous batching). The launch waits (bounded) on each slot's
 // readiness flag, which the slot's stream raises after binning, and reports a time-out to that
 // slot's status word only. With FP32 each slot rasterizes on its own stream.
 #include <algorithm>
@@ -74,6 +75,7 @@ struct Slot {
 };
 
 struct Batch {
+  cudaStream_t stream = nullptr;  // each launch its own stream: two run side by side
   cudaEvent_t done = nullptr;
   int* counter = nullptr;  // device work counter (tgs_rasterize_batch workspace)
   std::vector<int> slots;
@@ -97,7 +99,6 @@ struct tgs_server {
   std::atomic<int64_t> hbm{0};
   std::vector<tgs::Slot> slots;
   tgs::Batch batches[tgs::kMaxBatches];
-  cudaStream_t batch_stream = nullptr;
   void* batch_mem = nullptr;
   size_t slot_bytes = 0;
   std::atomic<bool> drained{true};
@@ -256,7 +257,7 @@ tgs_status launch_batch(tgs_server* S, int bi) {
   int count = 0;
   for (int k : b.slots) {
     Slot& sl = S->slots[k];
-    TGS_CUDA(cudaStreamWaitEvent(S->batch_stream, sl.done, 0));
+    TGS_CUDA(cudaStreamWaitEvent(b.stream, sl.done, 0));
     sl.host->status = TGS_OK;
     sl.host->done = 0;
     const Request& r = sl.req;
@@ -267,8 +268,10 @@ tgs_status launch_batch(tgs_server* S, int bi) {
   tgs_raster_opts o{};
   o.precision = S->cfg.precision;
   for (int k = 0; k < 3; ++k) o.bg[k] = S->cfg.bg[k];
+  // each launch takes at most half of the GPU's CTA slots, so that a launch of newly binned
+  // (often small) frames starts beside a running one instead of queueing behind it
   tgs_status s = launch_raster_tc_batch(rf, count, S->cfg.tiling.group_w, S->cfg.tiling.group_h, o,
-                                        b.counter, kReadyWaitNs, S->batch_stream);
+                                        b.counter, kReadyWaitNs, b.stream, kMaxBatches);
   if (s != TGS_OK) {
     b.slots.clear();
     return s;
@@ -277,7 +280,7 @@ tgs_status launch_batch(tgs_server* S, int bi) {
     S->slots[k].state = SlotState::kRaster;
     S->slots[k].batch = bi;
   }
-  TGS_CUDA(cudaEventRecord(b.done, S->batch_stream));
+  TGS_CUDA(cudaEventRecord(b.done, b.stream));
   b.busy = true;
   return TGS_OK;
 }
@@ -447,9 +450,10 @@ tgs_status tgs_serve_create(const tgs_serve_config* config, tgs_server** out) {
       if (t.host) cudaFreeHost(t.host);
       if (t.mem) cudaFree(t.mem);
     }
-    for (Batch& b : S->batches)
+    for (Batch& b : S->batches) {
       if (b.done) cudaEventDestroy(b.done);
-    if (S->batch_stream) cudaStreamDestroy(S->batch_stream);
+      if (b.stream) cudaStreamDestroy(b.stream);
+    }
     if (S->batch_mem) cudaFree(S->batch_mem);
     delete S;
     return cuda_status(e, what);
@@ -465,10 +469,10 @@ tgs_status tgs_serve_create(const tgs_serve_config* config, tgs_server** out) {
     e = cudaMemset(sl.words, 0, 16);
     if (e != cudaSuccess) return cleanup(e, "serving slot");
   }
-  cudaError_t e = cudaStreamCreateWithPriority(&S->batch_stream, cudaStreamNonBlocking, lo);
-  if (e == cudaSuccess) e = device_malloc(&S->batch_mem, batch_bytes);
+  cudaError_t e = device_malloc(&S->batch_mem, batch_bytes);
   for (int k = 0; e == cudaSuccess && k < kMaxBatches; ++k) {
-    e = cudaEventCreateWithFlags(&S->batches[k].done, cudaEventDisableTiming);
+    e = cudaStreamCreateWithPriority(&S->batches[k].stream, cudaStreamNonBlocking, lo);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->batches[k].done, cudaEventDisableTiming);
     S->batches[k].counter = reinterpret_cast<int*>(static_cast<char*>(S->batch_mem) + 256 * k);
   }
   if (e != cudaSuccess) return cleanup(e, "serving batch stream");
@@ -616,8 +620,10 @@ tgs_status tgs_serve_destroy(tgs_server* S) {
     cudaStreamDestroy(sl.stream);
     cudaEventDestroy(sl.done);
   }
-  for (Batch& b : S->batches) cudaEventDestroy(b.done);
-  cudaStreamDestroy(S->batch_stream);
+  for (Batch& b : S->batches) {
+    cudaEventDestroy(b.done);
+    cudaStreamDestroy(b.stream);
+  }
   if (drained) {
     cudaFree(S->batch_mem);
     for (auto& kv : S->scenes) cudaFree(kv.second.mem);

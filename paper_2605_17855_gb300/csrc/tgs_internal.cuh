@@ -71,12 +71,14 @@ struct RasterFrame {
   int32_t* done;
   int32_t done_value;
 };
+// share_div > 1 limits the persistent grid to 1/share_div of the GPU's resident CTA slots, so
+// that another launch can run beside it.
 tgs_status launch_raster_tc_batch(const RasterFrame* frames, int count, int gw, int gh,
                                   const tgs_raster_opts& o, int* next_item, uint64_t wait_ns,
-                                  cudaStream_t st);
+                                  cudaStream_t st, int share_div = 1);
 tgs_status launch_raster_tc_batch_bf16(const RasterFrame* frames, int count, int gw, int gh,
                                        const tgs_raster_opts& o, int* next_item, uint64_t wait_ns,
-                                       cudaStream_t st);
+                                       cudaStream_t st, int share_div);
 tgs_status launch_raster_backward(const tgs_projected& p, int64_t n, const tgs_bins& b, int width,
                                   int height, int gw, int gh, const tgs_raster_opts& o,
                                   const float* out_T, const int32_t* n_contrib, const float* grad_rgb,
