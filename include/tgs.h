@@ -167,7 +167,11 @@ tgs_status tgs_bin_sort_workspace_size(int64_t n, int64_t capacity, int32_t widt
  * is (0, 0) and *num_entries holds the needed count. If num_entries_host != NULL the call copies
  * the count to it, synchronizes `stream` and returns TGS_ERR_CAPACITY on overflow; otherwise it is
  * fully asynchronous. `workspace` is device memory of at least tgs_bin_sort_workspace_size bytes,
- * 256-byte aligned. */
+ * 256-byte aligned. The radix passes and prefixes wait on earlier tiles (decoupled look-back); a
+ * wait that outlasts the limit of tgs_set_lookback_limit records TGS_ERR_TIMEOUT in the device
+ * error word (tgs_last_device_error) and the call ends with empty bins (every range (0, 0),
+ * *num_entries 0), which rasterize to the background; with num_entries_host the call then returns
+ * TGS_ERR_TIMEOUT. */
 tgs_status tgs_bin_sort(const tgs_projected* proj, int64_t n, int32_t width, int32_t height,
                         const tgs_tiling* tiling, void* workspace, size_t workspace_bytes,
                         tgs_bins* bins, int64_t* num_entries_host, void* stream);
@@ -274,6 +278,13 @@ int64_t tgs_allocation_count(void);
 /* Device-side error word of the library on the current device (TGS_OK or TGS_ERR_TIMEOUT), set by
  * a kernel whose bounded wait expired. Synchronizes the device. reset != 0 clears it. */
 tgs_status tgs_last_device_error(int32_t reset);
+
+/* Sets the limit, in nanoseconds of the device's global timer, of one look-back wait of the bin
+ * sort (tgs_bin_sort, tgs_bin_sort_static and the service's binning) for the calls launched after
+ * it, process-wide; ns <= 0 restores the default of 1 s. A CUDA graph keeps the limit it was
+ * captured with. Returns the previous limit. A limit far below a tile's run time makes waits run
+ * out: a way to exercise the time-out path. */
+int64_t tgs_set_lookback_limit(int64_t ns);
 
 /* ---------------------------------------------------------------------------------------------
  * Rendering service (tgs_serve_*): resident scenes and asynchronous frame requests.

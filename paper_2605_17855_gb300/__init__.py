@@ -140,6 +140,7 @@ SIGNATURES = {
                                            C.c_int32, C.POINTER(_Tiling), C.POINTER(_RasterOpts), _P, _P,
                                            _P, _P, _P, _P, _P]),
     "tgs_last_device_error": (C.c_int32, [C.c_int32]),
+    "tgs_set_lookback_limit": (C.c_int64, [C.c_int64]),
     "tgs_kernel_launch_count": (C.c_int64, []),
     "tgs_allocation_count": (C.c_int64, []),
     "tgs_serve_create": (C.c_int32, [C.POINTER(_ServeConfig), C.POINTER(_P)]),
@@ -462,6 +463,12 @@ def last_device_error(reset=False) -> int:
     return int(load().tgs_last_device_error(1 if reset else 0))
 
 
+def set_lookback_limit(ns: int) -> int:
+    """Limit of one look-back wait of the bin sort for later calls (ns <= 0: the default, 1 s);
+    returns the previous limit (tgs_set_lookback_limit)."""
+    return int(load().tgs_set_lookback_limit(int(ns)))
+
+
 def render(scene: DeviceScene, camera, tiling=(2, 2), precision="fp16_tc", bg=(0.0, 0.0, 0.0),
            bins: Bins | None = None, sync=True, stream=None):
     """preprocess -> bin_sort -> rasterize. Returns (rgb, T, n_contrib, proj, bins)."""
@@ -509,15 +516,17 @@ class Renderer:
     (x `margin`); a frame that outgrows its capacity renders background only and reports it through
     `overflowed()`.
 
-    With `pipeline` (default) the preprocess + bin sort of a frame runs on a second stream with its
-    own buffer set (two sets, alternating by camera index), so it overlaps the rasterization of the
-    previous frame; each set is reused only after the rasterization that read it. Frames are enqueued
-    by render(); join() makes the current stream wait for every enqueued frame. Images are the same
-    as without the pipeline.
+    With `pipeline` (default) the preprocess + bin sort of a frame runs on a stream of its own buffer
+    set (`sets` sets, taken round robin by camera index), so the preprocess + bin sort chains of the
+    next `sets - 1` frames run side by side with each other and with the rasterization of the current
+    frame; each set is reused only after the rasterization that read it. Rasterizations run in frame
+    order on one stream. Frames are enqueued by render(); join() makes the current stream wait for
+    every enqueued frame. Images are the same as without the pipeline.
     """
 
     def __init__(self, scene: DeviceScene, cameras, tiling=(2, 2), precision="fp16_tc",
-                 bg=(0.0, 0.0, 0.0), margin=1.1, graphs=True, cull=True, pipeline=True, membership=True):
+                 bg=(0.0, 0.0, 0.0), margin=1.1, graphs=True, cull=True, pipeline=True, membership=True,
+                 sets=3):
         self.cull = cull
         self.membership = membership
         self.scene, self.cameras = scene, list(cameras)
@@ -525,7 +534,7 @@ class Renderer:
         self.pipeline = bool(pipeline)
         n = scene.n
         dev = scene.means.device
-        nsets = 2 if self.pipeline else 1
+        nsets = max(2, int(sets)) if self.pipeline else 1
         self.proj_sets = [Projected.empty(n, dev) for _ in range(nsets)]
         self.proj = self.proj_sets[0]
         cap = 0
@@ -547,7 +556,8 @@ class Renderer:
         # short kernels then takes SM slots as the current frame's raster CTAs retire, instead of
         # queueing behind the whole raster grid.
         top = torch.cuda.Stream.priority_range()[1]
-        self.s_prep = torch.cuda.Stream(device=dev, priority=top) if self.pipeline else None
+        self.s_prep = ([torch.cuda.Stream(device=dev, priority=top) for _ in range(nsets)]
+                       if self.pipeline else None)
         self.s_raster = torch.cuda.Stream(device=dev) if self.pipeline else None
         self._set_free = [None] * nsets  # event after the last rasterization that read each set
         for k in range(len(self.cameras)):  # run every path once outside capture
@@ -603,17 +613,18 @@ class Renderer:
         st = self._set(k)
         ready = torch.cuda.Event()
         ready.record(cur)  # the caller's work issued so far (e.g. a scene upload)
-        with torch.cuda.stream(self.s_prep):
-            self.s_prep.wait_event(ready)
+        sp = self.s_prep[st]
+        with torch.cuda.stream(sp):
+            sp.wait_event(ready)
             if self._set_free[st] is not None:
-                self.s_prep.wait_event(self._set_free[st])
+                sp.wait_event(self._set_free[st])
             if events:
-                events[0].record(self.s_prep)
+                events[0].record(sp)
             self.g_prep[k].replay() if self.g_prep else self._prep(k)
             prepped = torch.cuda.Event()
-            prepped.record(self.s_prep)
+            prepped.record(sp)
             if events:
-                events[1].record(self.s_prep)
+                events[1].record(sp)
         with torch.cuda.stream(self.s_raster):
             self.s_raster.wait_event(prepped)
             self.g_raster[k].replay() if self.g_raster else self._raster(k)
@@ -629,7 +640,8 @@ class Renderer:
         if self.pipeline:
             cur = torch.cuda.current_stream()
             cur.wait_stream(self.s_raster)
-            cur.wait_stream(self.s_prep)
+            for sp in self.s_prep:
+                cur.wait_stream(sp)
 
     def overflowed(self) -> bool:
         """True if the last frame of a buffer set needed more bin entries than the capacity

@@ -176,7 +176,17 @@ tgs_status tgs_bin_sort(const tgs_projected* proj, int64_t n, int32_t width, int
   if (s != TGS_OK || !num_entries_host) return s;
   TGS_CUDA(cudaMemcpyAsync(num_entries_host, bins->num_entries, sizeof(int64_t),
                            cudaMemcpyDeviceToHost, st));
+  int32_t failed = 0;
+  if (n > 0)
+    TGS_CUDA(cudaMemcpyAsync(&failed,
+                             bin_sort_failed_word(workspace, n, bins->capacity,
+                                                  group_cols(width, tiling), group_rows(height, tiling)),
+                             sizeof failed, cudaMemcpyDeviceToHost, st));
   TGS_CUDA(cudaStreamSynchronize(st));
+  if (failed) {
+    set_error("a look-back wait of the bin sort ran out: the bins are empty");
+    return TGS_ERR_TIMEOUT;
+  }
   if (*num_entries_host > bins->capacity) {
     set_error("frame needs %lld entries, capacity %lld", (long long)*num_entries_host,
               (long long)bins->capacity);
@@ -278,6 +288,8 @@ tgs_status tgs_rasterize_backward(const tgs_projected* proj, int64_t n, const tg
                                 *opts, out_T, n_contrib, grad_rgb, g_mean2d, g_conic_opacity, g_rgb,
                                 (cudaStream_t)stream);
 }
+
+int64_t tgs_set_lookback_limit(int64_t ns) { return set_lookback_limit_ns(ns); }
 
 tgs_status tgs_last_device_error(int32_t reset) {
   g_msg[0] = 0;

@@ -27,6 +27,7 @@
 // Every radix pass and the prefix are single kernels: a tile's offsets come from the earlier tiles
 // by decoupled look-back (bounded waits) instead of separate histogram and scan kernels.
 #include <algorithm>
+#include <atomic>
 
 #include "tgs_internal.cuh"
 
@@ -50,7 +51,20 @@ constexpr uint32_t kFlagPrefix = 2u << 30;  // the inclusive prefix up to the ti
 constexpr uint32_t kValMask = (1u << 30) - 1u;
 constexpr uint64_t kFlagAgg64 = 1ull << 62, kFlagPrefix64 = 2ull << 62;
 constexpr uint64_t kValMask64 = (1ull << 62) - 1ull;
-constexpr uint64_t kLookbackLimitNs = 1000000000ull;  // 1 s
+
+// The bounded waits of one bin sort call: where a wait that runs out is reported (the device error
+// word, sticky until read, and the call's own failure word in its workspace, cleared at the start of
+// every call), and the limit of one wait.
+struct WaitCtl {
+  int32_t* err;
+  int32_t* failed;
+  uint64_t limit_ns;
+};
+
+__device__ __forceinline__ void wait_expired(const WaitCtl& wc) {
+  if (wc.err) atomicExch(wc.err, TGS_ERR_TIMEOUT);
+  atomicExch(wc.failed, 1);
+}
 
 __device__ __forceinline__ int64_t live_count(const int64_t* count_dev, int64_t count_host,
                                               int64_t cap) {
@@ -95,11 +109,13 @@ __device__ __forceinline__ T block_excl_scan(T v, T* tmp, T* total = nullptr) {
 // inclusive prefix. The status words of up to kWindow earlier tiles are read at once (one memory
 // round trip per window). Tiles are numbered by an atomic ticket taken when the block starts, so
 // every earlier tile belongs to a block that is already running. A wait longer than the limit
-// records TGS_ERR_TIMEOUT and stops (the result is then wrong, but the kernel ends).
+// records TGS_ERR_TIMEOUT, marks the call failed and stops; the tile then publishes a prefix that is
+// short (never long), so every position derived from it stays below the true one, and the kernels
+// that follow turn the failed call into empty bins.
 constexpr int kWindow = 16;
 
 __device__ uint32_t lookback32(uint32_t* status, int tile, int slots, int d, uint32_t mine,
-                               int32_t* err) {
+                               const WaitCtl& wc) {
   volatile uint32_t* st = status;
   if (tile == 0) {
     st[d] = kFlagPrefix | mine;
@@ -130,8 +146,8 @@ __device__ uint32_t lookback32(uint32_t* status, int tile, int slots, int d, uin
     if (k == 0) {  // no progress in this round
       const uint64_t now = globaltimer_ns();
       if (t0 == 0) t0 = now;
-      if (now - t0 > kLookbackLimitNs) {
-        if (err) atomicExch(err, TGS_ERR_TIMEOUT);
+      if (now - t0 > wc.limit_ns) {
+        wait_expired(wc);
         break;
       }
     }
@@ -141,7 +157,7 @@ __device__ uint32_t lookback32(uint32_t* status, int tile, int slots, int d, uin
 }
 
 // The same for one 64-bit value per tile, done by one warp: lane k reads tile t - k.
-__device__ uint64_t lookback64_warp(uint64_t* status, int tile, uint64_t mine, int32_t* err) {
+__device__ uint64_t lookback64_warp(uint64_t* status, int tile, uint64_t mine, const WaitCtl& wc) {
   volatile uint64_t* st = status;
   const int lane = threadIdx.x & 31;
   if (tile == 0) {
@@ -171,8 +187,8 @@ __device__ uint64_t lookback64_warp(uint64_t* status, int tile, uint64_t mine, i
     if (used == 0) {
       const uint64_t now = __shfl_sync(0xffffffffu, globaltimer_ns(), 0);
       if (t0 == 0) t0 = now;
-      if (now - t0 > kLookbackLimitNs) {
-        if (lane == 0 && err) atomicExch(err, TGS_ERR_TIMEOUT);
+      if (now - t0 > wc.limit_ns) {
+        if (lane == 0) wait_expired(wc);
         break;
       }
     }
@@ -420,7 +436,7 @@ __global__ void __launch_bounds__(THREADS) k_onesweep(
     const uint16_t* __restrict__ masks_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, uint16_t* __restrict__ masks_out, const int64_t* count_dev,
     int64_t count_host, int64_t cap, int shift, const uint32_t* __restrict__ ghist,
-    uint32_t* __restrict__ status, int* __restrict__ tile_counter, int32_t* __restrict__ err) {
+    uint32_t* __restrict__ status, int* __restrict__ tile_counter, WaitCtl wc) {
   static_assert(THREADS % kRadix == 0, "THREADS must be a multiple of the digit count");
   constexpr int W = THREADS / 32;
   constexpr int TILE = THREADS * ITEMS;
@@ -483,7 +499,7 @@ __global__ void __launch_bounds__(THREADS) k_onesweep(
       total += c;
     }
   }
-  const uint32_t excl_tiles = digit_thread ? lookback32(status, tile, kRadix, d, total, err) : 0u;
+  const uint32_t excl_tiles = digit_thread ? lookback32(status, tile, kRadix, d, total, wc) : 0u;
   const uint32_t gstart = block_excl_scan<uint32_t, THREADS>(digit_thread ? ghist[d] : 0u, tmp);
   const uint32_t ds = block_excl_scan<uint32_t, THREADS>(total, tmp);
   if (digit_thread) {
@@ -519,13 +535,14 @@ template <int THREADS, int ITEMS, bool MASK>
 tgs_status launch_onesweep(int blocks, cudaStream_t st, const uint32_t* keys_in, const uint32_t* vals_in,
                            const uint16_t* masks_in, uint32_t* keys_out, uint32_t* vals_out,
                            uint16_t* masks_out, const int64_t* count_dev, int64_t cap, int shift,
-                           const uint32_t* ghist, uint32_t* status, int* tile_counter, int32_t* err) {
+                           const uint32_t* ghist, uint32_t* status, int* tile_counter,
+                           const WaitCtl& wc) {
   constexpr size_t smem = onesweep_smem_bytes<THREADS, ITEMS, MASK>();
   auto* k = k_onesweep<THREADS, ITEMS, MASK>;
   // static + dynamic shared memory may exceed the default 48 KB: opt in to the dynamic part
   TGS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k<<<blocks, THREADS, smem, st>>>(keys_in, vals_in, masks_in, keys_out, vals_out, masks_out,
-                                   count_dev, 0, cap, shift, ghist, status, tile_counter, err);
+                                   count_dev, 0, cap, shift, ghist, status, tile_counter, wc);
   TGS_CHECK_LAUNCH("k_onesweep");
   return TGS_OK;
 }
@@ -541,7 +558,7 @@ __global__ void __launch_bounds__(kSortThreads) k_depth_keys(
     int n, const int* __restrict__ radius, const float* __restrict__ depth,
     uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int64_t* __restrict__ visible,
     uint32_t* __restrict__ ghist, uint64_t* __restrict__ status, int* __restrict__ tile_counter,
-    int32_t* __restrict__ err) {
+    WaitCtl wc) {
   constexpr int W = kSortThreads / 32;
   __shared__ uint32_t h[W][4 * kRadix];
   __shared__ uint32_t cnt[kSortItems][W];  // visible items per (round, warp), then their offsets
@@ -600,7 +617,7 @@ __global__ void __launch_bounds__(kSortThreads) k_depth_keys(
       run += v[k];
     }
     const uint64_t tile_total = __shfl_sync(0xffffffffu, incl, 31);
-    const uint64_t pre = lookback64_warp(status, tile, tile_total, err);
+    const uint64_t pre = lookback64_warp(status, tile, tile_total, wc);
     if (threadIdx.x == 0) s_prefix = pre;
     if (base + kSortTile >= n && threadIdx.x == 0) *visible = (int64_t)(pre + tile_total);
   }
@@ -633,13 +650,17 @@ __global__ void __launch_bounds__(256) k_count_entries(
     const int64_t* __restrict__ visible, const uint32_t* __restrict__ order,
     const int4* __restrict__ rect, const float2* __restrict__ mean2d,
     const float4* __restrict__ conic_opacity, int gw_rt, int gh_rt, int use,
-    uint32_t* __restrict__ counts) {
+    const int32_t* __restrict__ failed, uint32_t* __restrict__ counts) {
   const int gw = GW > 0 ? GW : gw_rt, gh = GH > 0 ? GH : gh_rt;
   __shared__ WarpGauss sg_all[8][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = *visible;
   if (s - lane >= n) return;  // warp-uniform
+  if (*failed) {  // the depth order has holes: no entries
+    if (s < n) counts[s] = 0u;
+    return;
+  }
   const WarpGauss w = warp_gauss(s, n, order, rect, mean2d, conic_opacity, gh, use != 0);
   sg_all[warp][lane] = w;
   __syncwarp();
@@ -671,7 +692,7 @@ __global__ void __launch_bounds__(256) k_count_entries(
 __global__ void __launch_bounds__(kSortThreads) k_entry_offsets(
     const int64_t* __restrict__ visible, const uint32_t* __restrict__ counts,
     uint32_t* __restrict__ offsets, int64_t* __restrict__ total, uint64_t* __restrict__ status,
-    int* __restrict__ tile_counter, int32_t* __restrict__ err) {
+    int* __restrict__ tile_counter, WaitCtl wc) {
   __shared__ uint64_t tmp[kSortThreads / 32];
   __shared__ uint64_t s_prefix;
   __shared__ int s_tile;
@@ -700,7 +721,7 @@ __global__ void __launch_bounds__(kSortThreads) k_entry_offsets(
   uint64_t tile_total = 0;
   uint64_t run = block_excl_scan<uint64_t>(sum, tmp, &tile_total);
   if (threadIdx.x < 32) {
-    const uint64_t pre = lookback64_warp(status, tile, tile_total, err);
+    const uint64_t pre = lookback64_warp(status, tile, tile_total, wc);
     if (threadIdx.x == 0) s_prefix = pre;
   }
   __syncthreads();
@@ -724,8 +745,8 @@ __global__ void __launch_bounds__(256) k_emit(
     const int4* __restrict__ rect, const float2* __restrict__ mean2d,
     const float4* __restrict__ conic_opacity, const uint32_t* __restrict__ offsets,
     const int64_t* __restrict__ total_entries, int64_t cap, int gw_rt, int gh_rt, int GX, int use,
-    int passes, uint32_t* __restrict__ gkeys, uint32_t* __restrict__ vals,
-    uint16_t* __restrict__ masks, uint32_t* __restrict__ ghist) {
+    int passes, const int32_t* __restrict__ failed, uint32_t* __restrict__ gkeys,
+    uint32_t* __restrict__ vals, uint16_t* __restrict__ masks, uint32_t* __restrict__ ghist) {
   const int gw = GW > 0 ? GW : gw_rt, gh = GH > 0 ? GH : gh_rt;
   __shared__ uint32_t h[kMaxPasses * kRadix];
   __shared__ WarpGauss sg_all[8][32];
@@ -734,7 +755,7 @@ __global__ void __launch_bounds__(256) k_emit(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = *visible;
-  if (*total_entries <= cap && s - lane < n) {  // warp-uniform
+  if (*total_entries <= cap && s - lane < n && !*failed) {  // warp-uniform
     const WarpGauss w = warp_gauss(s, n, order, rect, mean2d, conic_opacity, gh, use != 0);
     sg_all[warp][lane] = w;
     __syncwarp();
@@ -797,11 +818,16 @@ __global__ void __launch_bounds__(256) k_emit(
 }
 
 // Group ranges from the sorted group ids ([start, end) at the first and past the last entry of
-// each group; the others stay (0, 0)) and the optional 64-bit keys.
-__global__ void k_ranges(const int64_t* __restrict__ total, int64_t cap,
+// each group; the others stay (0, 0)) and the optional 64-bit keys. A call whose look-back ran out
+// ends here with empty bins: no ranges and an entry count of 0.
+__global__ void k_ranges(int64_t* __restrict__ total, int64_t cap, const int32_t* __restrict__ failed,
                          const uint32_t* __restrict__ gkeys, const uint32_t* __restrict__ vals,
                          const float* __restrict__ depth, uint32_t* __restrict__ ranges,
                          uint64_t* __restrict__ keys64) {
+  if (*failed) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *total = 0;
+    return;
+  }
   const int64_t E = *total;
   if (E > cap) return;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
@@ -819,7 +845,8 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // (digit histograms, look-back status words, tile tickets).
 struct WsLayout {
   size_t dkA, dkB, dvA, dvB, counts, offs, gkA, gkB, gvB, gmB;
-  size_t zero_begin, hist_d, hist_g, stat_d, stat_g, stat_o, stat_c, tickets, visible, zero_end;
+  size_t zero_begin, hist_d, hist_g, stat_d, stat_g, stat_o, stat_c, tickets, visible, failed,
+      zero_end;
   int nb_c, nb_d, nb_g, nb_o;
   size_t total;
 };
@@ -863,6 +890,7 @@ WsLayout layout(int64_t n, int64_t cap, int GX, int GY) {
   L.stat_c = take(8 * (size_t)L.nb_c);
   L.tickets = take(4 * (4 + kMaxPasses + 2));
   L.visible = take(8);
+  L.failed = take(4);
   L.zero_end = off;
   L.total = off;
   return L;
@@ -872,6 +900,16 @@ WsLayout layout(int64_t n, int64_t cap, int GX, int GY) {
 
 size_t bin_sort_workspace_bytes(int64_t n, int64_t capacity, int GX, int GY) {
   return layout(n, capacity, GX, GY).total;
+}
+
+int32_t* bin_sort_failed_word(void* ws, int64_t n, int64_t capacity, int GX, int GY) {
+  return reinterpret_cast<int32_t*>(static_cast<char*>(ws) + layout(n, capacity, GX, GY).failed);
+}
+
+static std::atomic<int64_t> g_lookback_limit_ns{kDefaultLookbackLimitNs};
+
+int64_t set_lookback_limit_ns(int64_t ns) {
+  return g_lookback_limit_ns.exchange(ns > 0 ? ns : kDefaultLookbackLimitNs);
 }
 
 tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int height, int gw, int gh,
@@ -915,7 +953,9 @@ tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int h
   const int4* rect = reinterpret_cast<const int4*>(p.rect);
   const float2* m2 = reinterpret_cast<const float2*>(p.mean2d);
   const float4* co = reinterpret_cast<const float4*>(p.conic_opacity);
-  int32_t* err = err_word ? err_word : device_error_word();
+  auto* failed = reinterpret_cast<int32_t*>(w + L.failed);
+  const WaitCtl wc{err_word ? err_word : device_error_word(), failed,
+                   (uint64_t)g_lookback_limit_ns.load()};
   TGS_CUDA(cudaMemsetAsync(w + L.zero_begin, 0, L.zero_end - L.zero_begin, st));
 
   // 1. depth order of the visible Gaussians: compacted keys + digit histograms, then four
@@ -923,14 +963,14 @@ tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int h
   auto* visible = reinterpret_cast<int64_t*>(w + L.visible);
   auto* stat_c = reinterpret_cast<uint64_t*>(w + L.stat_c);
   k_depth_keys<<<L.nb_c, kSortThreads, 0, st>>>(n, p.radius, p.depth, dkA, dvA, visible, hist_d,
-                                                stat_c, tickets + 4 + kMaxPasses + 1, err);
+                                                stat_c, tickets + 4 + kMaxPasses + 1, wc);
   TGS_CHECK_LAUNCH("k_depth_keys");
   for (int pass = 0; pass < 4; ++pass) {
     const bool odd = pass & 1;
     const tgs_status s = launch_onesweep<kDepthThreads, kDepthItems, false>(
         L.nb_d, st, odd ? dkB : dkA, odd ? dvB : dvA, nullptr, odd ? dkA : dkB, odd ? dvA : dvB,
         nullptr, visible, n, 8 * pass, hist_d + pass * kRadix,
-        stat_d + (size_t)pass * L.nb_d * kRadix, tickets + pass, err);
+        stat_d + (size_t)pass * L.nb_d * kRadix, tickets + pass, wc);
     if (s != TGS_OK) return s;
   }
   const uint32_t* order = dvA;  // after an even number of passes
@@ -943,10 +983,10 @@ tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int h
                     : grp == 42 ? k_count_entries<4, 2> : grp == 24 ? k_count_entries<2, 4>
                     : grp == 44 ? k_count_entries<4, 4> : k_count_entries<0, 0>;
   count_kernel<<<div_up(n, 256), 256, 0, st>>>(visible, order, rect, m2, co, gw, gh,
-                                               membership ? 1 : 0, counts);
+                                               membership ? 1 : 0, failed, counts);
   TGS_CHECK_LAUNCH("k_count_entries");
   k_entry_offsets<<<L.nb_o, kSortThreads, 0, st>>>(visible, counts, offs, b.num_entries, stat_o,
-                                                   tickets + 4 + kMaxPasses, err);
+                                                   tickets + 4 + kMaxPasses, wc);
   TGS_CHECK_LAUNCH("k_entry_offsets");
   if (cap == 0) return TGS_OK;
 
@@ -962,8 +1002,8 @@ tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int h
   auto emit_kernel = grp == 11 ? k_emit<1, 1> : grp == 22 ? k_emit<2, 2> : grp == 42 ? k_emit<4, 2>
                    : grp == 24 ? k_emit<2, 4> : grp == 44 ? k_emit<4, 4> : k_emit<0, 0>;
   emit_kernel<<<div_up(n, 256), 256, 0, st>>>(visible, order, rect, m2, co, offs, b.num_entries, cap,
-                                               gw, gh, GX, membership ? 1 : 0, passes, ek, ev, em,
-                                               hist_g);
+                                               gw, gh, GX, membership ? 1 : 0, passes, failed, ek,
+                                               ev, em, hist_g);
   TGS_CHECK_LAUNCH("k_emit");
 
   // 4. stable sort by group id, carrying index and mask
@@ -973,14 +1013,15 @@ tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int h
     const tgs_status s = launch_onesweep<kGidThreads, kGidItems, true>(
         L.nb_g, st, odd ? ok : ek, odd ? ov : ev, odd ? om : em, odd ? ek : ok, odd ? ev : ov,
         odd ? em : om, b.num_entries, cap, 8 * pass, hist_g + pass * kRadix,
-        stat_g + (size_t)pass * L.nb_g * kRadix, tickets + 4 + pass, err);
+        stat_g + (size_t)pass * L.nb_g * kRadix, tickets + 4 + pass, wc);
     if (s != TGS_OK) return s;
     gk = odd ? ek : ok;
   }
 
   // 5. group ranges and the optional 64-bit keys
   const int rng_blocks = std::max(1, std::min(div_up(cap, 256), 152 * 16));
-  k_ranges<<<rng_blocks, 256, 0, st>>>(b.num_entries, cap, gk, b.vals, p.depth, b.ranges, b.keys);
+  k_ranges<<<rng_blocks, 256, 0, st>>>(b.num_entries, cap, failed, gk, b.vals, p.depth, b.ranges,
+                                       b.keys);
   TGS_CHECK_LAUNCH("k_ranges");
   return TGS_OK;
 }

@@ -155,7 +155,7 @@ __device__ __forceinline__ int64_t floor_div_tile(int64_t v) {
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(256, 4) k_preprocess(int n, const float* __restrict__ means,
+__global__ void __launch_bounds__(128, 8) k_preprocess(int n, const float* __restrict__ means,
                                                     const float* __restrict__ scales,
                                                     const float4* __restrict__ quats,
                                                     const float* __restrict__ opac,
@@ -262,7 +262,7 @@ tgs_status launch_preprocess(const tgs_scene& s, const tgs_camera& cam, const tg
     return TGS_ERR_INVALID_ARGUMENT;
   }
   const int n = (int)s.n;
-  const int threads = 256, blocks = div_up(n, threads);
+  const int threads = 128, blocks = div_up(n, threads);
   auto* q4 = reinterpret_cast<const float4*>(s.quats);
   auto* m2 = reinterpret_cast<float2*>(out.mean2d);
   auto* co = reinterpret_cast<float4*>(out.conic_opacity);

@@ -45,6 +45,12 @@ inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 tgs_status launch_preprocess(const tgs_scene& s, const tgs_camera& cam, const tgs_projected& out,
                              cudaStream_t st);
 size_t bin_sort_workspace_bytes(int64_t n, int64_t capacity, int GX, int GY);
+// The word of a bin sort workspace that a call sets when one of its look-back waits ran out (n > 0).
+int32_t* bin_sort_failed_word(void* ws, int64_t n, int64_t capacity, int GX, int GY);
+// The limit of one look-back wait of the bin sort for calls launched after it; ns <= 0 restores the
+// default. Returns the previous limit.
+constexpr int64_t kDefaultLookbackLimitNs = 1000000000;  // 1 s
+int64_t set_lookback_limit_ns(int64_t ns);
 // err_word: the device word its bounded waits report to (NULL: the library's error word).
 tgs_status launch_bin_sort(const tgs_projected& p, int64_t n, int width, int height, int gw, int gh,
                            bool membership, void* ws, size_t ws_bytes, const tgs_bins& bins,
