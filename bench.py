@@ -27,6 +27,7 @@ import subprocess
 import sys
 import threading
 import time
+import types
 
 import numpy as np
 
@@ -732,31 +733,25 @@ def main():
     pairs, exps, _ = [int(v) / ncam for v in cnt_plain.cpu().tolist()]
     pairs_main, _, slots = [int(v) / ncam for v in cnt_main.cpu().tolist()]
 
-    # end to end through the C ABI: every step copies the scene host -> device from pinned memory,
-    # calls tgs_preprocess, tgs_bin_sort and tgs_rasterize per camera on one stream, and copies
-    # each image device -> host into pinned memory
+    # end to end through the C ABI with host buffers: every step is one tgs_frames_render call that
+    # uploads the scene from pinned host memory and renders the eight cameras into pinned host images
+    # (the copies overlap the kernels: two device scene copies, three frame buffer sets in flight)
     host = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32)).pin_memory()
             for k in ("means", "scales", "quats", "opacities", "sh")}
-    host_imgs = [torch.empty((3, H, W), dtype=torch.float32).pin_memory() for _ in cams]
+    host_scene = types.SimpleNamespace(sh_degree=scene.sh_degree, **host)
+    host_imgs = torch.empty((ncam, 3, H, W), dtype=torch.float32).pin_memory()
     h2d = sum(t.numel() * 4 for t in host.values())
-    d2h = sum(t.numel() * 4 for t in host_imgs)
-    e_proj = tgs.Projected.empty(scene.n)
-    e_bins = tgs.allocate_bins(scene.n, int(max(ent_main, 1) / ncam * 1.5) + 4096, W, H, tiling, keys=False)
-    e_out = [(torch.empty((3, H, W), device="cuda"), torch.empty((H, W), device="cuda")) for _ in cams]
+    d2h = host_imgs.numel() * 4
+    frames = tgs.Frames(scene.n, max_size=(W, H), max_entries=int(max(ent_main, 1) / ncam * 1.5) + 4096,
+                        tiling=tiling, precision=args.precision, sets=3, max_sh_degree=scene.sh_degree,
+                        device=local)
 
     def e2e_step():
-        for k, t in host.items():
-            getattr(ds, k).copy_(t, non_blocking=True)
-        for i, cam in enumerate(cams):
-            tgs.preprocess(ds, cam, out=e_proj)
-            tgs.bin_sort(e_proj, W, H, tiling, bins=e_bins, sync=False)
-            tgs.rasterize(e_proj, e_bins, W, H, args.precision, out=(e_out[i][0], e_out[i][1], None),
-                          want_n_contrib=False)
-            host_imgs[i].copy_(e_out[i][0], non_blocking=True)
+        frames.render(host_scene, cams, host_imgs, stream=stream)
 
     for _ in range(2):
         e2e_step()
-    torch.cuda.synchronize()
+    frames.wait()
     e2e_steps = max(3, args.steps // 2)
     a, b = ev(), ev()
     a.record(stream)
@@ -764,9 +759,9 @@ def main():
         e2e_step()
     b.record(stream)
     torch.cuda.synchronize()
+    frames.wait()  # raises on a capacity overflow or a bin-sort time-out
+    frames.close()
     clocks = sampler.stop()
-    if int(e_bins.num_entries.item()) > e_bins.capacity:
-        raise RuntimeError("bin capacity overflow in the end-to-end loop")
     e2e_ms = max_over_ranks(a.elapsed_time(b) / e2e_steps, dist, "cuda")
     e2e_value = whole_job_rate(ws, px_per_step, e2e_ms)
 
@@ -831,9 +826,10 @@ def main():
            "evals_per_s": round(pairs * ncam / (ms_per_step * 1e-3), 1),
            "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4),
-                   "how": "per step: scene copied host -> device (pinned), tgs_preprocess, tgs_bin_sort and "
-                          "tgs_rasterize called per camera through the C ABI on one stream, each image copied "
-                          "device -> host (pinned)"},
+                   "how": "per step: one tgs_frames_render call (C ABI, host buffers): the scene uploaded "
+                          "from pinned host memory, preprocess -> bin sort -> rasterize per camera, every image "
+                          "downloaded into pinned host memory; copies overlapped with the kernels (two device "
+                          "scene copies, three frame buffer sets in flight)"},
            "gpu_launches": launches,
            "kernels_per_frame": R["main"][0].kernels_per_frame[0],
            "graphs": "one CUDA graph pair per camera (preprocess + bin sort, rasterize); the preprocess + "
@@ -856,7 +852,7 @@ def main():
         # the other workloads of the evaluation, in the same run: 6M Gaussians at 3840x2160 (grouping
         # x precision autotune with its error against the oracle), forward + backward, and the
         # rendering service under a sweep of offered rates
-        del R, rs, e_proj, e_bins, e_out, ds
+        del R, rs, frames, ds
         torch.cuda.empty_cache()
         import argparse as _ap
         sub = _ap.Namespace(**vars(args))

@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define TGS_ABI_VERSION 2
+#define TGS_ABI_VERSION 3
 #define TGS_TILE 16
 #define TGS_MAX_GROUP 4
 
@@ -385,6 +385,64 @@ tgs_status tgs_serve_get_stats(tgs_server* server, tgs_serve_stats* out);
 /* Stops the worker, waits (bounded) for the frames in slots, frees all device memory and the
  * server. Requests still queued are dropped. */
 tgs_status tgs_serve_destroy(tgs_server* server);
+
+/* ---------------------------------------------------------------------------------------------
+ * Frame sequences from host memory (tgs_frames_*): a scene in host memory rendered from a list of
+ * cameras into host images, every frame the Section 2 pipeline (tgs_preprocess -> tgs_bin_sort ->
+ * tgs_rasterize), with the host <-> device copies overlapped with the frames' kernels.
+ *
+ * A tgs_frames object owns two device copies of a scene, `sets` buffer sets (projected
+ * attributes, bins with their workspace, one image) and its streams: one for uploads, one per
+ * buffer set for preprocess + bin sort (of the highest priority), one for rasterization (frames in
+ * order) and one for downloads. Each call uploads the scene into the copy the previous call did
+ * not use, so one call's upload overlaps the previous call's frames; frame k of a call takes
+ * buffer set (frames enqueued before it) % sets, which is reused once its image has been
+ * downloaded. Every buffer is allocated by tgs_frames_create; the calls allocate nothing. An
+ * object is used by one host thread at a time and must not be used after destroy. */
+
+typedef struct {
+  int64_t max_gaussians;         /* largest scene (1 .. 2^30 - 1) */
+  int32_t max_sh_degree;         /* largest SH degree of a scene (0..3) */
+  int32_t max_width, max_height; /* largest frame (1 .. 16384 each) */
+  int64_t max_entries;           /* bin entries a frame may need (1 .. 2^30 - 1); a frame that needs
+                                    more renders the background and tgs_frames_wait reports
+                                    TGS_ERR_CAPACITY */
+  tgs_tiling tiling;             /* tile grouping (and binning flags) of every frame */
+  int32_t precision;             /* TGS_PRECISION_* */
+  float bg[3];                   /* background colour */
+  int32_t sets;                  /* buffer sets = frames in flight (2..8) */
+  int32_t device;                /* CUDA device ordinal (must be sm_103) */
+} tgs_frames_config;
+
+typedef struct tgs_frames tgs_frames; /* opaque */
+
+/* Allocates the object's device buffers (on config->device) and streams. INVALID_ARGUMENT for a
+ * bad config, UNSUPPORTED_DEVICE off sm_103, CUDA when an allocation fails (nothing is kept). */
+tgs_status tgs_frames_create(const tgs_frames_config* config, tgs_frames** out);
+
+/* Device bytes the object holds. */
+int64_t tgs_frames_device_bytes(const tgs_frames* frames);
+
+/* Enqueues one call and returns: the upload of `scene` (host arrays, [n,...] as tgs_scene; page-
+ * locked memory makes the copies asynchronous), then for every camera k (all of one size) the
+ * frame's kernels and the download of its image into out_rgb + k * 3 * H * W (host, [count,3,H,W])
+ * and, if out_T != NULL, of its transmittance into out_T + k * H * W. The host arrays must stay
+ * untouched until the call has completed: tgs_frames_wait, or work enqueued afterwards on `stream`
+ * (which is made to wait for the call; NULL = the default stream). INVALID_ARGUMENT for NULL
+ * pointers, a scene or frame larger than the config's, cameras of different sizes, count < 0;
+ * count = 0 does nothing. */
+tgs_status tgs_frames_render(tgs_frames* frames, const tgs_scene* scene, const tgs_camera* cams,
+                             int32_t count, float* out_rgb, float* out_T, void* stream);
+
+/* Blocks until every call enqueued so far has completed. Returns TGS_ERR_CAPACITY if a frame since
+ * the last wait needed more than max_entries bin entries (its image is the background),
+ * TGS_ERR_TIMEOUT if a bounded wait of the bin sort ran out (that frame's bins were empty), else
+ * TGS_OK; the conditions are cleared. Time-outs of the rasterizer's own waits are reported by
+ * tgs_last_device_error, as for tgs_rasterize. */
+tgs_status tgs_frames_wait(tgs_frames* frames);
+
+/* Waits for the object's work, then frees its buffers, streams and the object. */
+tgs_status tgs_frames_destroy(tgs_frames* frames);
 
 #ifdef __cplusplus
 }

@@ -107,6 +107,13 @@ class _ServeConfig(C.Structure):
 SERVE_MAX_RESOLUTIONS = 16
 
 
+class _FramesConfig(C.Structure):
+    _fields_ = [("max_gaussians", C.c_int64), ("max_sh_degree", C.c_int32), ("max_width", C.c_int32),
+                ("max_height", C.c_int32), ("max_entries", C.c_int64), ("tiling", _Tiling),
+                ("precision", C.c_int32), ("bg", C.c_float * 3), ("sets", C.c_int32),
+                ("device", C.c_int32)]
+
+
 class _ServeResolutionStats(C.Structure):
     _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("completed", C.c_int64),
                 ("mean_ms", C.c_double), ("p50_ms", C.c_double), ("p99_ms", C.c_double)]
@@ -152,6 +159,11 @@ SIGNATURES = {
     "tgs_serve_pause": (C.c_int32, [_P, C.c_int32]),
     "tgs_serve_get_stats": (C.c_int32, [_P, C.POINTER(_ServeStats)]),
     "tgs_serve_destroy": (C.c_int32, [_P]),
+    "tgs_frames_create": (C.c_int32, [C.POINTER(_FramesConfig), C.POINTER(_P)]),
+    "tgs_frames_device_bytes": (C.c_int64, [_P]),
+    "tgs_frames_render": (C.c_int32, [_P, C.POINTER(_Scene), C.POINTER(_Camera), C.c_int32, _P, _P, _P]),
+    "tgs_frames_wait": (C.c_int32, [_P]),
+    "tgs_frames_destroy": (C.c_int32, [_P]),
 }
 
 
@@ -753,3 +765,89 @@ class Server:
     def __exit__(self, *exc):
         self.close()
 
+
+
+# ------------------------------------------------------------------------------------------------
+# Frame sequences from host memory
+
+def _host_f32(a):
+    """A contiguous float32 host array (numpy or CPU torch tensor) and its address."""
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous():
+            raise ValueError("host arrays must be contiguous float32 CPU tensors")
+        return a, a.data_ptr()
+    a = np.ascontiguousarray(a, np.float32)
+    return a, a.ctypes.data
+
+
+class Frames:
+    """A tgs_frames object (include/tgs.h, tgs_frames_*): a scene in host memory rendered from a
+    list of cameras into host images, the host <-> device copies overlapped with the kernels (two
+    device copies of the scene, `sets` buffer sets in flight). Every buffer is allocated here.
+    Use as a context manager or call close()."""
+
+    def __init__(self, max_gaussians: int, max_size=(1920, 1080), max_entries: int = 1 << 22,
+                 tiling=(2, 2), precision: str = "fp16_tc", bg=(0.0, 0.0, 0.0), sets: int = 3,
+                 max_sh_degree: int = 3, device: int = 0, membership: bool = True):
+        lib = load()
+        cfg = _FramesConfig(int(max_gaussians), int(max_sh_degree), int(max_size[0]), int(max_size[1]),
+                            int(max_entries), _tiling(tiling, membership), PRECISION[precision],
+                            (C.c_float * 3)(*[float(v) for v in bg]), int(sets), int(device))
+        h = _P()
+        _check(lib.tgs_frames_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+        self._keep = []  # host arrays of calls not yet waited for
+
+    def _handle(self):
+        if self._h is None:
+            raise TgsError(TGS_ERR_INVALID_ARGUMENT, "frames object closed")
+        return self._h
+
+    @property
+    def device_bytes(self) -> int:
+        return int(load().tgs_frames_device_bytes(self._handle()))
+
+    def render(self, scene, cams, out_rgb, out_T=None, stream=None):
+        """Enqueues one call: `scene` has host arrays means, scales, quats, opacities, sh (numpy or
+        CPU tensors; page-locked CPU tensors make the copies asynchronous) and sh_degree; out_rgb is
+        a host float32 [len(cams), 3, H, W] (out_T [len(cams), H, W] or None). The arrays are kept
+        alive until wait(). `stream` (a torch CUDA stream; None = the default stream) is made to wait
+        for the call."""
+        cams = list(cams)
+        arrs = [_host_f32(getattr(scene, k)) for k in ("means", "scales", "quats", "opacities", "sh")]
+        n = int(np.prod(arrs[0][0].shape)) // 3
+        st = _Scene(n, int(scene.sh_degree), *[p if n else None for _, p in arrs])
+        cs = (_Camera * max(1, len(cams)))(*[camera_struct(c) for c in cams])
+        rgb, prgb = _host_f32(out_rgb)
+        T, pT = _host_f32(out_T) if out_T is not None else (None, None)
+        if rgb is not out_rgb or (out_T is not None and T is not out_T):
+            raise ValueError("out_rgb / out_T must be contiguous float32 host arrays (written in place)")
+        s = C.c_void_p(stream.cuda_stream) if stream is not None else None
+        _check(load().tgs_frames_render(self._handle(), C.byref(st), cs, len(cams), prgb, pT, s))
+        self._keep.append((arrs, rgb, T))
+
+    def wait(self):
+        """Blocks until every enqueued call has completed; raises TgsError (CAPACITY, TIMEOUT) as
+        tgs_frames_wait reports."""
+        try:
+            _check(load().tgs_frames_wait(self._handle()))
+        finally:
+            self._keep.clear()
+
+    def close(self):
+        if self._h is not None:
+            _check(load().tgs_frames_destroy(self._h))
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -819,17 +819,21 @@ __global__ void __launch_bounds__(256) k_emit(
 
 // Group ranges from the sorted group ids ([start, end) at the first and past the last entry of
 // each group; the others stay (0, 0)) and the optional 64-bit keys. A call whose look-back ran out
-// ends here with empty bins: no ranges and an entry count of 0.
+// ends here with empty bins: no ranges and an entry count of 0. A frame that needs more entries
+// than the capacity sets the optional overflow word.
 __global__ void k_ranges(int64_t* __restrict__ total, int64_t cap, const int32_t* __restrict__ failed,
                          const uint32_t* __restrict__ gkeys, const uint32_t* __restrict__ vals,
                          const float* __restrict__ depth, uint32_t* __restrict__ ranges,
-                         uint64_t* __restrict__ keys64) {
+                         uint64_t* __restrict__ keys64, int32_t* __restrict__ overflow) {
   if (*failed) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *total = 0;
     return;
   }
   const int64_t E = *total;
-  if (E > cap) return;
+  if (E > cap) {
+    if (overflow && blockIdx.x == 0 && threadIdx.x == 0) atomicExch(overflow, 1);
+    return;
+  }
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t g = gkeys[e];
@@ -914,7 +918,7 @@ int64_t set_lookback_limit_ns(int64_t ns) {
 
 tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int height, int gw, int gh,
                            bool membership, void* ws, size_t ws_bytes, const tgs_bins& b,
-                           cudaStream_t st, int32_t* err_word) {
+                           cudaStream_t st, int32_t* err_word, int32_t* overflow_word) {
   (void)ws_bytes;
   const int n = (int)n64;
   const int TX = div_up(width, kTile), TY = div_up(height, kTile);
@@ -1021,7 +1025,7 @@ tgs_status launch_bin_sort(const tgs_projected& p, int64_t n64, int width, int h
   // 5. group ranges and the optional 64-bit keys
   const int rng_blocks = std::max(1, std::min(div_up(cap, 256), 152 * 16));
   k_ranges<<<rng_blocks, 256, 0, st>>>(b.num_entries, cap, failed, gk, b.vals, p.depth, b.ranges,
-                                       b.keys);
+                                       b.keys, overflow_word);
   TGS_CHECK_LAUNCH("k_ranges");
   return TGS_OK;
 }

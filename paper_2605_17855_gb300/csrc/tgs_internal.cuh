@@ -51,10 +51,12 @@ int32_t* bin_sort_failed_word(void* ws, int64_t n, int64_t capacity, int GX, int
 // default. Returns the previous limit.
 constexpr int64_t kDefaultLookbackLimitNs = 1000000000;  // 1 s
 int64_t set_lookback_limit_ns(int64_t ns);
-// err_word: the device word its bounded waits report to (NULL: the library's error word).
+// err_word: the device word its bounded waits report to (NULL: the library's error word);
+// overflow_word: optional device word set to 1 when the frame needs more entries than the capacity.
 tgs_status launch_bin_sort(const tgs_projected& p, int64_t n, int width, int height, int gw, int gh,
                            bool membership, void* ws, size_t ws_bytes, const tgs_bins& bins,
-                           cudaStream_t st, int32_t* err_word = nullptr);
+                           cudaStream_t st, int32_t* err_word = nullptr,
+                           int32_t* overflow_word = nullptr);
 tgs_status launch_raster_fp32(const tgs_projected& p, const tgs_bins& b, int width, int height,
                               int gw, int gh, const tgs_raster_opts& o, float* out_rgb, float* out_T,
                               int32_t* n_contrib, cudaStream_t st);

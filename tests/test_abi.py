@@ -45,7 +45,7 @@ def test_library_exports_every_declared_function(lib):
 
 
 def test_status_strings_and_version(lib):
-    assert lib.tgs_abi_version() == 2
+    assert lib.tgs_abi_version() == 3
     assert lib.tgs_status_string(0) == b"TGS_OK"
     assert lib.tgs_status_string(3) == b"TGS_ERR_CAPACITY"
     assert lib.tgs_status_string(99) == b"TGS_ERR_UNKNOWN"

@@ -409,15 +409,17 @@ def test_autograd_function():
     assert math.isfinite(float(loss))
 
 
-@pytest.mark.parametrize("pipeline", [True, False])
-def test_renderer_frames_equal_direct_path(pipeline):
-    # the CUDA-graph renderer (with and without the two-stream pipeline and its alternating buffer
-    # sets) produces exactly the frames of the direct preprocess -> bin sort -> rasterize calls
+@pytest.mark.parametrize("pipeline,sets", [(True, 2), (True, 3), (True, 5), (False, 1)])
+def test_renderer_frames_equal_direct_path(pipeline, sets):
+    # the CUDA-graph renderer (with and without the multi-stream pipeline; buffer sets reused by
+    # later cameras, or one per camera) produces exactly the frames of the direct
+    # preprocess -> bin sort -> rasterize calls
     scene = scenes.mixture_scene(40_000, seed=31, components=32, cluster_std=0.3, radius=2.0,
                                  log_scale_mean=-3.8, sh_degree=3, needle_fraction=0.05)
     cams = scenes.orbit_cameras(8, 5.0, 320, 240)[:5]
     ds = tgs.DeviceScene.from_host(scene)
-    rend = tgs.Renderer(ds, cams, (2, 2), "fp16_tc", pipeline=pipeline)
+    rend = tgs.Renderer(ds, cams, (2, 2), "fp16_tc", pipeline=pipeline, sets=sets)
+    assert len(rend.proj_sets) == (sets if pipeline else 1)
     for _ in range(2):
         for i in range(len(cams)):
             rend.render(i)
