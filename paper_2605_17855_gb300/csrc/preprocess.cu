@@ -15,10 +15,6 @@ struct CamParams {
   float near_z, limx, limy;
 };
 
-// Near-degenerate covariances (det < 2^-5 Sxx Syy) are recomputed in FP64: the FP32 determinant
-// loses ~kappa * 2^-24 relative accuracy, kappa = Sxx Syy / det.
-constexpr float kDegenerateRatio = 1.0f / 32.0f;
-
 __device__ __forceinline__ void quat_rot_f32(float4 q, float Rq[9]) {
   const float inv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
   const float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
@@ -28,9 +24,14 @@ __device__ __forceinline__ void quat_rot_f32(float4 q, float Rq[9]) {
 }
 
 // 2D covariance (without dilation) as the Gram matrix of T3 = J W Rq S, the projected scaled axes:
-// Sigma' = J W (Rq S)(Rq S)^T W^T J^T = T3 T3^T.
-__device__ void cov2d_f32(const CamParams& c, float3 pc, float4 q, float3 s, float& cxx, float& cxy,
-                          float& cyy) {
+// Sigma' = J W (Rq S)(Rq S)^T W^T J^T = T3 T3^T, and its determinant. By Lagrange's identity the
+// determinant of a Gram matrix is |t0 x t1|^2 (t0, t1 the rows of T3), and with t_i = M j_i,
+// M = S Rq^T W^T, the cofactor identity (M u) x (M v) = cof(M) (u x v) gives
+// t0 x t1 = diag(s1 s2, s0 s2, s0 s1) Rq^T W^T (j0 x j1) (rotations are their own cofactors):
+// products and rotations only, so the determinant keeps FP32 relative accuracy however thin the
+// projected ellipse, where Sxx Syy - Sxy^2 would cancel.
+__device__ __forceinline__ void cov2d_f32(const CamParams& c, float3 pc, float4 q, float3 s,
+                                          float& cxx, float& cxy, float& cyy, float& det) {
   float Rq[9];
   quat_rot_f32(q, Rq);
   const float z = pc.z, iz = 1.f / z;
@@ -54,45 +55,15 @@ __device__ void cov2d_f32(const CamParams& c, float3 pc, float4 q, float3 s, flo
   cxx = T0[0] * T0[0] + T0[1] * T0[1] + T0[2] * T0[2];
   cxy = T0[0] * T1[0] + T0[1] * T1[1] + T0[2] * T1[2];
   cyy = T1[0] * T1[0] + T1[1] * T1[1] + T1[2] * T1[2];
-}
-
-// Same quantity in FP64 from the same FP32 inputs (used only for near-degenerate splats).
-// Returns (Sxx, Sxy, Syy) by value and takes the mean by value, so that no caller variable has to
-// live in local memory around the call.
-__device__ __noinline__ double3 cov2d_f64(const CamParams& c, float3 mv, float4 qf, float3 s) {
-  const float m[3] = {mv.x, mv.y, mv.z};
-  double pc[3];
+  // j0 = (j00, 0, j02), j1 = (0, j11, j12): j0 x j1 = (-j02 j11, -j00 j12, j00 j11)
+  const float n[3] = {-j02 * j11, -j00 * j12, j00 * j11};
+  float v[3], w[3];
 #pragma unroll
-  for (int r = 0; r < 3; ++r)
-    pc[r] = (double)c.R[3 * r] * m[0] + (double)c.R[3 * r + 1] * m[1] + (double)c.R[3 * r + 2] * m[2] +
-            (double)c.t[r];
-  const double nq = sqrt((double)qf.x * qf.x + (double)qf.y * qf.y + (double)qf.z * qf.z +
-                         (double)qf.w * qf.w);
-  const double w = qf.x / nq, x = qf.y / nq, y = qf.z / nq, z = qf.w / nq;
-  const double Rq[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
-                        2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
-                        2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
-  const double iz = 1.0 / pc[2];
-  double xz = pc[0] * iz, yz = pc[1] * iz;
-  const double lx = 1.3 * 0.5 * c.width / (double)c.fx, ly = 1.3 * 0.5 * c.height / (double)c.fy;
-  xz = fmin(fmax(xz, -lx), lx);
-  yz = fmin(fmax(yz, -ly), ly);
-  const double j00 = c.fx * iz, j02 = -(double)c.fx * xz * iz;
-  const double j11 = c.fy * iz, j12 = -(double)c.fy * yz * iz;
-  double JW[6];
-  for (int k = 0; k < 3; ++k) {
-    JW[k] = j00 * c.R[k] + j02 * c.R[6 + k];
-    JW[3 + k] = j11 * c.R[3 + k] + j12 * c.R[6 + k];
-  }
-  const double sv[3] = {s.x, s.y, s.z};
-  double T0[3], T1[3];
-  for (int col = 0; col < 3; ++col) {
-    T0[col] = (JW[0] * Rq[col] + JW[1] * Rq[3 + col] + JW[2] * Rq[6 + col]) * sv[col];
-    T1[col] = (JW[3] * Rq[col] + JW[4] * Rq[3 + col] + JW[5] * Rq[6 + col]) * sv[col];
-  }
-  return make_double3(T0[0] * T0[0] + T0[1] * T0[1] + T0[2] * T0[2],
-                      T0[0] * T1[0] + T0[1] * T1[1] + T0[2] * T1[2],
-                      T1[0] * T1[0] + T1[1] * T1[1] + T1[2] * T1[2]);
+  for (int k = 0; k < 3; ++k) v[k] = c.R[k] * n[0] + c.R[3 + k] * n[1] + c.R[6 + k] * n[2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) w[k] = Rq[k] * v[0] + Rq[3 + k] * v[1] + Rq[6 + k] * v[2];
+  const float d0 = s.y * s.z * w[0], d1 = s.x * s.z * w[1], d2 = s.x * s.y * w[2];
+  det = d0 * d0 + d1 * d1 + d2 * d2;
 }
 
 // Real SH basis up to degree 3 (index l*l + m + l), Condon-Shortley phase kept in the real form.
@@ -185,25 +156,13 @@ __global__ void __launch_bounds__(128, 8) k_preprocess(int n, const float* __res
   if (pc.z > c.near_z) {
     const float4 q = quats[i];
     const float3 s = make_float3(scales[3 * i], scales[3 * i + 1], scales[3 * i + 2]);
-    float cxx, cxy, cyy;
-    cov2d_f32(c, pc, q, s, cxx, cxy, cyy);
+    float cxx, cxy, cyy, det;
+    cov2d_f32(c, pc, q, s, cxx, cxy, cyy, det);
+    // dilation by 0.3 I: det(S + 0.3 I) = det S + 0.3 tr S + 0.09, a sum of non-negative terms
+    det = det + 0.3f * (cxx + cyy) + 0.09f;
     cxx += 0.3f;
     cyy += 0.3f;
-    float det = cxx * cyy - cxy * cxy;
-    float ca, cb, cc;
-    if (!(det >= kDegenerateRatio * cxx * cyy)) {
-      const double3 dc = cov2d_f64(c, make_float3(m[0], m[1], m[2]), q, s);
-      double dxx = dc.x, dxy = dc.y, dyy = dc.z;
-      dxx += 0.3;
-      dyy += 0.3;
-      const double ddet = dxx * dyy - dxy * dxy;
-      cxx = (float)dxx; cxy = (float)dxy; cyy = (float)dyy;
-      det = (float)ddet;
-      ca = (float)(dyy / ddet); cb = (float)(-dxy / ddet); cc = (float)(dxx / ddet);
-      if (!(ddet > 0.0)) det = 0.f;
-    } else {
-      ca = cyy / det; cb = -cxy / det; cc = cxx / det;
-    }
+    const float ca = cyy / det, cb = -cxy / det, cc = cxx / det;
     if (det > 0.f) {
       const float mx = c.fx * pc.x / pc.z + c.cx;
       const float my = c.fy * pc.y / pc.z + c.cy;

@@ -79,10 +79,21 @@ def _mixture_small():
     return scene, cam
 
 
+def _needles():
+    # half of the splats 400:1 needles: long, thin projected ellipses whose covariance is nearly
+    # singular (Sxx Syy - Sxy^2 would cancel in FP32)
+    scene = scenes.mixture_scene(3000, seed=41, components=4, cluster_std=0.2, radius=0.8,
+                                 log_scale_mean=-2.5, log_scale_std=0.3, sh_degree=0,
+                                 needle_fraction=0.5, needle_ratio=400.0)
+    cam = scenes.orbit_cameras(4, 3.0, 256, 192)[1]
+    return scene, cam
+
+
 CASES = {
     "box2k": lambda: (lambda s, c: (s, c[0]))(*scenes.box_2k_128()),
     "ragged": _ragged,
     "mixture": _mixture_small,
+    "needles": _needles,
 }
 
 
@@ -110,7 +121,8 @@ def test_preprocess_matches_oracle(case):
     np.testing.assert_allclose(p["depth"][both], o.depth[both], rtol=1e-6)
     np.testing.assert_allclose(p["opacity"][both], o.opacity[both], rtol=0, atol=0)
     np.testing.assert_allclose(p["rgb"][both], o.rgb[both], rtol=1e-5, atol=1e-5)
-    # conic: relative to its largest entry (the FP64 branch keeps near-degenerate ones accurate)
+    # conic: relative to its largest entry (the determinant from the cross product of the projected
+    # axes keeps near-degenerate ones accurate in FP32)
     scale = np.abs(o.conic[both]).max(axis=1, keepdims=True)
     err = np.abs(p["conic"][both] - o.conic[both]) / scale
     assert err.max() < 2e-5, err.max()
