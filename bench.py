@@ -705,7 +705,7 @@ def main():
     tgs.bin_sort(rs.proj, W, H, tiling, bins=rs.bins, sync=False)
     e[2].record(stream)
     torch.cuda.synchronize()
-    stages = {"note": "the headline path without the two-stream pipeline (CUDA events between the stages)",
+    stages = {"note": "the headline path without the frame pipeline (CUDA events between the stages)",
               "value_without_pipeline": paths["main"]["value_without_pipeline"],
               "preprocess_plus_bin_sort_ms": paths["main"]["preprocess_plus_bin_sort_ms"],
               "rasterize_ms": paths["main"]["rasterize_ms"],
