@@ -1120,8 +1120,12 @@ tgs_status launch_batch_cfg(const RasterFrame* frames, int count, const tgs_rast
   smem = std::max(smem, (size_t)smem_sm / (max_ctas + 1) - 1024 + 16);
   auto* k = k_raster_tc_batch<GW, GH, NWG, NPROD, NST, BF>;
   TGS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int occ = 0;
-  TGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, Cf::kThreads, smem));
+  // the residency the kernel is built for (its launch bounds and shared-memory floor): two CTAs
+  // per SM with one accumulator stage. The occupancy query is not used: it assumes the default
+  // L1 / shared-memory split, under which it reports one CTA per SM, while the driver picks the
+  // split that fits two (as for the single-frame launch); a persistent grid of half the CTAs was
+  // 1.4x slower.
+  const int occ = 2 / NST;
   const int64_t slots = std::max<int64_t>(1, (int64_t)std::max(occ, 1) * sms / std::max(share_div, 1));
   const int grid = (int)std::min<int64_t>(std::max<int64_t>(total, 1), slots);
   TGS_CUDA(cudaMemsetAsync(next_item, 0, sizeof(int) * (1 + kMaxBatchFrames), st));
