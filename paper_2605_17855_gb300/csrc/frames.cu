@@ -186,9 +186,8 @@ tgs_status tgs_frames_create(const tgs_frames_config* config, tgs_frames** out) 
   cudaError_t e = device_malloc(&F->mem, F->bytes);
   if (e != cudaSuccess) return fail(e, "frames buffers");
   layout(F, true);
-  e = cudaMemset(F->words, 0, 16);
   const unsigned flags = cudaStreamNonBlocking;
-  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&F->upload, flags, lo);
+  e = cudaStreamCreateWithPriority(&F->upload, flags, lo);
   if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&F->raster, flags, lo);
   if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&F->download, flags, lo);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&F->done, cudaEventDisableTiming);
@@ -202,7 +201,9 @@ tgs_status tgs_frames_create(const tgs_frames_config* config, tgs_frames** out) 
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.drawn, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.free, cudaEventDisableTiming);
   }
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();  // the memset is complete
+  // the status words start at 0 (ordered before every later call by the upload stream's events)
+  if (e == cudaSuccess) e = cudaMemsetAsync(F->words, 0, 16, F->upload);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(F->upload);
   if (e != cudaSuccess) return fail(e, "frames streams");
   *out = F;
   return TGS_OK;
