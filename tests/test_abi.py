@@ -128,6 +128,39 @@ def test_serve_argument_validation_is_host_side(lib):
     assert lib.tgs_serve_destroy(None) == tgs.TGS_ERR_INVALID_ARGUMENT
 
 
+def test_frames_argument_validation_is_host_side(lib):
+    import ctypes as C
+
+    import paper_2605_17855_gb300 as tgs
+    h = C.c_void_p()
+
+    def cfg(**kw):
+        f = dict(max_gaussians=1000, max_sh_degree=3, max_width=64, max_height=64, max_entries=4096,
+                 tiling=tgs._Tiling(2, 2, 0), precision=1, bg=(C.c_float * 3)(0, 0, 0), sets=3,
+                 device=0)
+        f.update(kw)
+        return tgs._FramesConfig(**f)
+
+    assert lib.tgs_frames_create(None, C.byref(h)) == tgs.TGS_ERR_INVALID_ARGUMENT
+    for bad in (cfg(sets=1), cfg(sets=9), cfg(max_gaussians=0), cfg(max_sh_degree=4),
+                cfg(max_width=0), cfg(max_height=20000), cfg(max_entries=0), cfg(precision=7),
+                cfg(tiling=tgs._Tiling(5, 1, 0)), cfg(tiling=tgs._Tiling(2, 2, 8))):
+        assert lib.tgs_frames_create(C.byref(bad), C.byref(h)) == tgs.TGS_ERR_INVALID_ARGUMENT
+        assert not h.value  # nothing was created
+    assert lib.tgs_frames_render(None, None, None, 0, None, None, None) == tgs.TGS_ERR_INVALID_ARGUMENT
+    assert lib.tgs_frames_wait(None) == tgs.TGS_ERR_INVALID_ARGUMENT
+    assert lib.tgs_frames_destroy(None) == tgs.TGS_ERR_INVALID_ARGUMENT
+    assert lib.tgs_frames_device_bytes(None) == 0
+
+
+def test_lookback_limit_setting(lib):
+    # process-wide host setting: returns the previous limit, <= 0 restores the default of 1 s
+    default = 1_000_000_000
+    assert lib.tgs_set_lookback_limit(5000) == default
+    assert lib.tgs_set_lookback_limit(0) == 5000
+    assert lib.tgs_set_lookback_limit(-3) == default
+    assert lib.tgs_set_lookback_limit(default) == default
+
 
 def test_size_limits_are_checked_on_the_host(lib):
     import ctypes as C
