@@ -1057,13 +1057,14 @@ tgs_status launch_raster_tc_typed(const tgs_projected& p, const tgs_bins& b, int
                                   float* out_T, int32_t* n_contrib, cudaStream_t st) {
   if (((uintptr_t)p.mean2d & 7) || ((uintptr_t)p.conic_opacity & 15))
     return set_error("mean2d needs 8-byte and conic_opacity 16-byte alignment"), TGS_ERR_INVALID_ARGUMENT;
-  // FP16 groups of up to 8 tiles: one accumulator stage of 256 tensor-memory columns and at most
-  // 48 registers, so that two CTAs share an SM and hide each other's latency (measured faster than
-  // one CTA with two stages); 1x1 (not limited by tensor memory), 4x4 and BF16 (shared memory for
-  // two CTAs) keep two stages
+  // FP16 groups of up to 8 tiles and BF16 2x2 (about 83 KB of shared memory): one accumulator
+  // stage of 256 tensor-memory columns and at most 48 registers, so that two CTAs share an SM and
+  // hide each other's latency (measured faster than one CTA with two stages; BF16 2x2: 0.315 vs
+  // 0.422 ms per 1.5M-Gaussian 1600x1064 frame). 1x1 (not limited by tensor memory), 4x4, and
+  // BF16 4x2 / 2x4 (about 148 KB of shared memory: one CTA per SM) keep two stages
   constexpr int NST = BF ? 2 : 1;
   if (gw == 1 && gh == 1) return launch_cfg<BF, 1, 1, 1, 2>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
-  if (gw == 2 && gh == 2) return launch_cfg<BF, 2, 2, 4, 3, NST>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
+  if (gw == 2 && gh == 2) return launch_cfg<BF, 2, 2, 4, 3, 1>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
   if (gw == 4 && gh == 2) return launch_cfg<BF, 4, 2, 4, 3, NST>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
   if (gw == 2 && gh == 4) return launch_cfg<BF, 2, 4, 4, 3, NST>(p, b, width, height, o, out_rgb, out_T, n_contrib, st);
   // 4x4 BF16: two producers (four slots), so that the doubled coefficient tiles fit in shared memory
@@ -1142,7 +1143,7 @@ tgs_status launch_raster_tc_batch_typed(const RasterFrame* frames, int count, in
                                         cudaStream_t st, int share_div) {
   constexpr int NST = BF ? 2 : 1;  // the configurations of the single-frame launch
   if (gw == 1 && gh == 1) return launch_batch_cfg<BF, 1, 1, 1, 2>(frames, count, o, next_item, wait_ns, st, share_div);
-  if (gw == 2 && gh == 2) return launch_batch_cfg<BF, 2, 2, 4, 3, NST>(frames, count, o, next_item, wait_ns, st, share_div);
+  if (gw == 2 && gh == 2) return launch_batch_cfg<BF, 2, 2, 4, 3, 1>(frames, count, o, next_item, wait_ns, st, share_div);
   if (gw == 4 && gh == 2) return launch_batch_cfg<BF, 4, 2, 4, 3, NST>(frames, count, o, next_item, wait_ns, st, share_div);
   if (gw == 2 && gh == 4) return launch_batch_cfg<BF, 2, 4, 4, 3, NST>(frames, count, o, next_item, wait_ns, st, share_div);
   if (gw == 4 && gh == 4)
