@@ -733,6 +733,15 @@ __device__ __forceinline__ void raster_group(
                 blend_granule<TILES, KB, COUNT, NC, 4, decltype(scalar_rows)::value>(
                     ga, g, cnt, sb, base, sl, t, tx, ty, quarter, lane, mean2d, conic_opacity,
                     ps[r][0], ps[r][1], evaluated, passing, slots);
+                // after every second granule: a warp whose 64 pixels have all finished releases the
+                // stage and leaves the job (checking after every granule costs more than it saves)
+                if ((g & 1) && g + 1 < ngr4 &&
+                    __all_sync(0xffffffffu, ps[r][0].thr == inf_f() && ps[r][1].thr == inf_f())) {
+                  tc_fence_before();
+                  __syncwarp();
+                  if (lane == 0) mbar_arrive(&S.tempty[st]);
+                  break;
+                }
               }
             };
             if (sb)
