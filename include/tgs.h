@@ -313,7 +313,8 @@ typedef struct {
   int32_t slots;              /* frames in flight (1..16), each with its own buffers */
   int32_t device;             /* CUDA device ordinal (must be sm_103) */
   int32_t precision;          /* TGS_PRECISION_* */
-  tgs_tiling tiling;          /* tile grouping (and binning flags) of every frame */
+  tgs_tiling tiling;          /* tile grouping (and binning flags) of every frame; the tensor-core
+                                 precisions take 1x1, 2x2, 4x2, 2x4 or 4x4 groups */
   float bg[3];                /* background colour */
   int32_t request_timeout_ms; /* 0 = no limit */
   int64_t max_gaussians;      /* largest scene a slot renders (1 .. 2^30 - 1) */
@@ -407,7 +408,8 @@ typedef struct {
   int64_t max_entries;           /* bin entries a frame may need (1 .. 2^30 - 1); a frame that needs
                                     more renders the background and tgs_frames_wait reports
                                     TGS_ERR_CAPACITY */
-  tgs_tiling tiling;             /* tile grouping (and binning flags) of every frame */
+  tgs_tiling tiling;             /* tile grouping (and binning flags) of every frame; the tensor-core
+                                    precisions take 1x1, 2x2, 4x2, 2x4 or 4x4 groups */
   int32_t precision;             /* TGS_PRECISION_* */
   float bg[3];                   /* background colour */
   int32_t sets;                  /* buffer sets = frames in flight (2..8) */
@@ -430,7 +432,9 @@ int64_t tgs_frames_device_bytes(const tgs_frames* frames);
  * untouched until the call has completed: tgs_frames_wait, or work enqueued afterwards on `stream`
  * (which is made to wait for the call; NULL = the default stream). INVALID_ARGUMENT for NULL
  * pointers, a scene or frame larger than the config's, cameras of different sizes, count < 0;
- * count = 0 does nothing. */
+ * count = 0 does nothing. A launch that fails ends the call with its status after the frames
+ * before it; the call's events are still recorded, so later calls and `stream` are ordered after
+ * everything it enqueued. */
 tgs_status tgs_frames_render(tgs_frames* frames, const tgs_scene* scene, const tgs_camera* cams,
                              int32_t count, float* out_rgb, float* out_T, void* stream);
 

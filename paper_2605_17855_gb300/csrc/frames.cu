@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "groupings.h"
 #include "tgs_internal.cuh"
 
 namespace tgs {
@@ -150,10 +151,10 @@ bool valid_config(const tgs_frames_config& c) {
   return c.max_gaussians >= 1 && c.max_gaussians < (int64_t(1) << 30) && c.max_sh_degree >= 0 &&
          c.max_sh_degree <= 3 && c.max_width >= 1 && c.max_width <= 16384 && c.max_height >= 1 &&
          c.max_height <= 16384 && c.max_entries >= 1 && c.max_entries < (int64_t(1) << 30) &&
-         c.tiling.group_w >= 1 && c.tiling.group_w <= TGS_MAX_GROUP && c.tiling.group_h >= 1 &&
-         c.tiling.group_h <= TGS_MAX_GROUP && (c.tiling.flags & ~TGS_BIN_RANGE_ONLY) == 0 &&
+         (c.tiling.flags & ~TGS_BIN_RANGE_ONLY) == 0 &&
          (c.precision == TGS_PRECISION_FP32 || c.precision == TGS_PRECISION_FP16_TC ||
           c.precision == TGS_PRECISION_BF16_TC) &&
+         grouping_supported(c.precision, c.tiling.group_w, c.tiling.group_h) &&
          c.sets >= 2 && c.sets <= kMaxSets;
 }
 
@@ -262,34 +263,37 @@ tgs_status tgs_frames_render(tgs_frames* F, const tgs_scene* scene, const tgs_ca
   const bool membership = (c.tiling.flags & TGS_BIN_RANGE_ONLY) == 0;
   const int gw = c.tiling.group_w, gh = c.tiling.group_h;
   const size_t px = (size_t)W * H;
-  for (int k = 0; k < count; ++k) {
+  // A launch that fails stops the call, but the frame's events are still recorded and the call is
+  // closed as a complete one would be, so the next call waits for whatever this one enqueued.
+  tgs_status s = TGS_OK;
+  for (int k = 0; k < count && s == TGS_OK; ++k) {
     FrameSet& f = F->sets[F->frames % (int64_t)F->sets.size()];
     ++F->frames;
     // preprocess + bin sort once the scene is in and the set's previous image has been copied out
     // (which follows the rasterization that read the set's bins)
     TGS_CUDA(cudaStreamWaitEvent(f.prep, F->scene_in[b], 0));
     if (f.used) TGS_CUDA(cudaStreamWaitEvent(f.prep, f.free, 0));
-    tgs_status s = TGS_OK;
     if (n > 0) s = launch_preprocess(ds, cams[k], f.proj, f.prep);
     if (s == TGS_OK)
       s = launch_bin_sort(f.proj, n, W, H, gw, gh, membership, f.ws, f.ws_bytes, f.bins, f.prep,
                           F->words, F->words + 1);
-    if (s != TGS_OK) return s;
     TGS_CUDA(cudaEventRecord(f.prepped, f.prep));
     // rasterize in frame order
     TGS_CUDA(cudaStreamWaitEvent(F->raster, f.prepped, 0));
-    s = c.precision == TGS_PRECISION_FP32
-            ? launch_raster_fp32(f.proj, f.bins, W, H, gw, gh, o, f.rgb, f.T, nullptr, F->raster)
-            : launch_raster_tc(f.proj, f.bins, W, H, gw, gh, o, f.rgb, f.T, nullptr, F->raster);
-    if (s != TGS_OK) return s;
+    if (s == TGS_OK)
+      s = c.precision == TGS_PRECISION_FP32
+              ? launch_raster_fp32(f.proj, f.bins, W, H, gw, gh, o, f.rgb, f.T, nullptr, F->raster)
+              : launch_raster_tc(f.proj, f.bins, W, H, gw, gh, o, f.rgb, f.T, nullptr, F->raster);
     TGS_CUDA(cudaEventRecord(f.drawn, F->raster));
     // download
     TGS_CUDA(cudaStreamWaitEvent(F->download, f.drawn, 0));
-    TGS_CUDA(cudaMemcpyAsync(out_rgb + (size_t)k * 3 * px, f.rgb, 12 * px, cudaMemcpyDeviceToHost,
-                             F->download));
-    if (out_T)
-      TGS_CUDA(cudaMemcpyAsync(out_T + (size_t)k * px, f.T, 4 * px, cudaMemcpyDeviceToHost,
-                               F->download));
+    if (s == TGS_OK) {
+      TGS_CUDA(cudaMemcpyAsync(out_rgb + (size_t)k * 3 * px, f.rgb, 12 * px,
+                               cudaMemcpyDeviceToHost, F->download));
+      if (out_T)
+        TGS_CUDA(cudaMemcpyAsync(out_T + (size_t)k * px, f.T, 4 * px, cudaMemcpyDeviceToHost,
+                                 F->download));
+    }
     TGS_CUDA(cudaEventRecord(f.free, F->download));
     f.used = true;
   }
@@ -301,7 +305,7 @@ tgs_status tgs_frames_render(tgs_frames* F, const tgs_scene* scene, const tgs_ca
   // the caller's stream (NULL: the default stream) waits for the call
   TGS_CUDA(cudaStreamWaitEvent(static_cast<cudaStream_t>(stream), F->done, 0));
   ++F->calls;
-  return TGS_OK;
+  return s;
 }
 
 tgs_status tgs_frames_wait(tgs_frames* F) {

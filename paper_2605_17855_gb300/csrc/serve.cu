@@ -21,6 +21,7 @@
 #include <thread>
 #include <unordered_map>
 
+#include "groupings.h"
 #include "serve_core.h"
 #include "tgs_internal.cuh"
 
@@ -419,8 +420,8 @@ tgs_status tgs_serve_create(const tgs_serve_config* config, tgs_server** out) {
   if (c.max_inflight < 1 || c.slots < 1 || c.slots > kMaxSlots || c.hbm_budget_bytes <= 0 ||
       (c.precision != TGS_PRECISION_FP32 && c.precision != TGS_PRECISION_FP16_TC &&
        c.precision != TGS_PRECISION_BF16_TC) ||
-      c.tiling.group_w < 1 || c.tiling.group_w > TGS_MAX_GROUP || c.tiling.group_h < 1 ||
-      c.tiling.group_h > TGS_MAX_GROUP || (c.tiling.flags & ~TGS_BIN_RANGE_ONLY) != 0 ||
+      !grouping_supported(c.precision, c.tiling.group_w, c.tiling.group_h) ||
+      (c.tiling.flags & ~TGS_BIN_RANGE_ONLY) != 0 ||
       c.request_timeout_ms < 0 || c.max_gaussians < 1 || c.max_gaussians >= (int64_t(1) << 30) ||
       c.max_width < 1 || c.max_width > 16384 || c.max_height < 1 || c.max_height > 16384 ||
       c.max_entries < 1 || c.max_entries >= (int64_t(1) << 30))

@@ -123,6 +123,20 @@ def test_serve_argument_validation_is_host_side(lib):
     bad = tgs._ServeConfig(1 << 30, 4, 17, 0, 1, tgs._Tiling(2, 2), (C.c_float * 3)(0, 0, 0), 0)
     assert lib.tgs_serve_create(C.byref(bad), C.byref(h)) == tgs.TGS_ERR_INVALID_ARGUMENT
     assert lib.tgs_serve_create(None, C.byref(h)) == tgs.TGS_ERR_INVALID_ARGUMENT
+
+    def full(precision, gw, gh):  # complete apart from the grouping under test
+        return tgs._ServeConfig(1 << 30, 4, 2, 0, precision, tgs._Tiling(gw, gh, 0),
+                                (C.c_float * 3)(0, 0, 0), 0, 1000, 64, 64, 4096)
+
+    # groupings the tensor-core rasterizer is not built for are refused before any device work
+    for prec, gw, gh in ((1, 3, 1), (1, 1, 2), (2, 4, 1), (1, 5, 1), (0, 0, 1)):
+        assert lib.tgs_serve_create(C.byref(full(prec, gw, gh)), C.byref(h)) == tgs.TGS_ERR_INVALID_ARGUMENT
+        assert not h.value
+    for prec, gw, gh in ((1, 2, 2), (2, 4, 4), (0, 3, 1)):  # accepted: fails later without a GPU
+        s = lib.tgs_serve_create(C.byref(full(prec, gw, gh)), C.byref(h))
+        assert s != tgs.TGS_ERR_INVALID_ARGUMENT
+        if s == tgs.TGS_OK:
+            assert lib.tgs_serve_destroy(h) == tgs.TGS_OK
     st = tgs._ServeStats()
     assert lib.tgs_serve_get_stats(None, C.byref(st)) == tgs.TGS_ERR_INVALID_ARGUMENT
     assert lib.tgs_serve_destroy(None) == tgs.TGS_ERR_INVALID_ARGUMENT
@@ -144,9 +158,16 @@ def test_frames_argument_validation_is_host_side(lib):
     assert lib.tgs_frames_create(None, C.byref(h)) == tgs.TGS_ERR_INVALID_ARGUMENT
     for bad in (cfg(sets=1), cfg(sets=9), cfg(max_gaussians=0), cfg(max_sh_degree=4),
                 cfg(max_width=0), cfg(max_height=20000), cfg(max_entries=0), cfg(precision=7),
-                cfg(tiling=tgs._Tiling(5, 1, 0)), cfg(tiling=tgs._Tiling(2, 2, 8))):
+                cfg(tiling=tgs._Tiling(5, 1, 0)), cfg(tiling=tgs._Tiling(2, 2, 8)),
+                # groupings the tensor-core rasterizer is not built for
+                cfg(tiling=tgs._Tiling(3, 1, 0)), cfg(precision=2, tiling=tgs._Tiling(1, 2, 0))):
         assert lib.tgs_frames_create(C.byref(bad), C.byref(h)) == tgs.TGS_ERR_INVALID_ARGUMENT
         assert not h.value  # nothing was created
+    for good in (cfg(), cfg(precision=0, tiling=tgs._Tiling(3, 1, 0))):  # fails later without a GPU
+        s = lib.tgs_frames_create(C.byref(good), C.byref(h))
+        assert s != tgs.TGS_ERR_INVALID_ARGUMENT
+        if s == tgs.TGS_OK:
+            assert lib.tgs_frames_destroy(h) == tgs.TGS_OK
     assert lib.tgs_frames_render(None, None, None, 0, None, None, None) == tgs.TGS_ERR_INVALID_ARGUMENT
     assert lib.tgs_frames_wait(None) == tgs.TGS_ERR_INVALID_ARGUMENT
     assert lib.tgs_frames_destroy(None) == tgs.TGS_ERR_INVALID_ARGUMENT
